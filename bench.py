@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-profile sweep (distance-matrix cells per second).
+
+Workload (default): the pure-Euclidean matrix profile (AAMP, Algorithm 1) of
+a float32 random walk of n = 2^20 samples with 20 Gaussian bumps, m = 256,
+exclusion zone m / 4 = 64: N = 1,048,321 windows and 549,420,844,896 cells
+(unordered pairs with |i - j| > 64).  A step is one full mp_aamp call on
+device-resident T: conversion, diagonal sweep, FP64 polish, P and I.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank computes its own
+series (seed + rank): weak scaling, no collective on the data path.
+--impl reference times the FP64 CPU oracle (Algorithm 1, OpenMP over the
+host cores) on a bounded diagonal range of the same series.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1901_05708_gb300 import workloads as W  # noqa: E402
+
+METRIC = "distance-matrix cells/s (AAMP FP32 sweep, re-anchored, FP64-polished P)"
+UNIT = "GCells/s"
+FP32_INSTR_PER_CELL = 4          # minimum FP32-pipe instructions per cell (Lemma 1 update)
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples taken while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(series: W.Series, target_s: float = 12.0):
+    """Time the FP64 oracle (Algorithm 1, all host cores) on a diagonal range
+    of the series sized to take about target_s seconds."""
+    import oracle
+    oracle.build()
+    T = series.T.astype(np.float64)
+    k0 = series.excl + 1
+    # calibrate on a short range
+    kc = 256
+    t0 = time.perf_counter()
+    oracle.aamp(T, series.m, series.excl, k_range=(k0, k0 + kc))
+    dt = time.perf_counter() - t0
+    rate = kc * series.N / max(dt, 1e-6)  # cells/s, roughly
+    K = int(min(series.N - k0, max(kc, target_s * rate / series.N)))
+    t0 = time.perf_counter()
+    oracle.aamp(T, series.m, series.excl, k_range=(k0, k0 + K))
+    dt = time.perf_counter() - t0
+    cells = sum(series.N - k for k in range(k0, k0 + K))
+    return {"value": cells / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{series.name}: diagonals {k0}..{k0 + K - 1} ({cells:.3e} cells) in {dt:.2f} s",
+            "seconds": dt, "cells": cells}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    series = W.aamp_1m(seed=1)
+    runs = []
+    for _ in range(max(0, args.warmup_ref)):
+        oracle_sample(series, target_s=2.0)
+    for _ in range(args.steps):
+        runs.append(oracle_sample(series, target_s=args.ref_seconds))
+    cells = sum(r["cells"] for r in runs)
+    secs = sum(r["seconds"] for r in runs)
+    value = cells / secs / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, len(runs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(series),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": runs[0]["cores"], "kind": "oracle",
+                             "sample": runs[0]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(series: W.Series) -> dict:
+    return {"workload": f"{series.name} (AAMP pure Euclidean, float32 random walk + 20 Gaussian bumps)",
+            "n": series.n, "m": series.m, "excl": series.excl, "N": series.N,
+            "cells_per_step": series.cells, "precision": "fp32 sweep re-anchored every 64 rows, fp64 polish",
+            "l2": "flushed before every timed step (512 MiB write)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--warmup-ref", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=1 << 20)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1901_05708_gb300 import mp
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = mp.load()
+
+    series = W.aamp_1m(seed=1 + rank, n=args.n)
+    T_host = torch.from_numpy(series.T).pin_memory()
+    T = T_host.to(dev)
+    N = series.N
+    P = torch.empty(N, dtype=torch.float64, device=dev)
+    I = torch.empty(N, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        mp.aamp(T, series.m, series.excl, out=(P, I))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    mp.sync_status()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sw = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for a, b in sw:  # create the CUDA events now (torch makes them on first record)
+        a.record(stream)
+        b.record(stream)
+    clocks = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = lib.mp_launch_count()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)  # L2 flush, outside the timed events
+        lib.mp_set_sweep_events(ctypes_event(sw[k][0]), ctypes_event(sw[k][1]))
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    lib.mp_set_sweep_events(None, None)
+    torch.cuda.synchronize()
+    launches = lib.mp_launch_count() - launches0
+    clk = clocks.stop()
+    mp.sync_status()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    sweep_ms = [a.elapsed_time(b) for a, b in sw]
+    total_ms = float(sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+
+    cells = series.cells
+    value = ws * cells * args.steps / (total_ms * 1e-3) / 1e9
+
+    # ---- end to end through the public API with host buffers -------------------
+    P_host = torch.empty(N, dtype=torch.float64).pin_memory()
+    I_host = torch.empty(N, dtype=torch.int64).pin_memory()
+    T_dev2 = torch.empty_like(T)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        T_dev2.copy_(T_host, non_blocking=True)
+        mp.aamp(T_dev2, series.m, series.excl, out=(P, I))
+        P_host.copy_(P, non_blocking=True)
+        I_host.copy_(I, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_value = ws * cells / (e2e_ms * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel (the diagonal sweep) ------------------------
+    pk, src = peaks()
+    f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_cells = sms * FP32_LANES_PER_SM * f_max / FP32_INSTR_PER_CELL / 1e9
+    sweep_avg_ms = float(np.mean(sweep_ms))
+    achieved = cells / (sweep_avg_ms * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_cells, "unit": UNIT,
+            "frac": achieved / peak_cells, "traffic": None,
+            "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {f_max/1e6:.0f} MHz "
+                           f"({src} sm_max_mhz) / {FP32_INSTR_PER_CELL} FP32 instructions per cell",
+            "kernel": "mpk::sweep_kernel<K_P2,false>", "kernel_ms": sweep_avg_ms}
+    if clk.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (sms * FP32_LANES_PER_SM * clk["sm_mhz"] * 1e6
+                                                     / FP32_INSTR_PER_CELL / 1e9)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(series), "roofline": roof, "clocks": clk,
+            "gpu_launches": int(launches),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(T_host.numel() * 4),
+                    "d2h_bytes_per_step": int(N * 16), "ms_per_step": e2e_ms}}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample(series, target_s=args.ref_seconds)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def ctypes_event(e):
+    """The cudaEvent_t handle of a (recorded) torch.cuda.Event as a void*."""
+    import ctypes
+    h = getattr(e, "cuda_event", 0)
+    if not h:
+        raise RuntimeError("torch.cuda.Event has no CUDA handle yet")
+    return ctypes.c_void_p(h)
+
+
+if __name__ == "__main__":
+    main()

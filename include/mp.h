@@ -1,0 +1,152 @@
+/*
+ * mp.h -- C ABI of the GB300 matrix-profile library (libmp.so).
+ *
+ * The library computes the matrix profile P and its index I of a time series
+ * (Akbarinia & Cloez, arXiv:1901.05708):
+ *
+ *   Def. 2.2  subsequence T_{i,m} = <t_i .. t_{i+m-1}>, 0 <= i < N = n-m+1
+ *   Def. 2.4  P[i] = min_j d(i, j),  I[i] = argmin_j d(i, j)
+ *
+ * over all j with |i - j| > excl (the exclusion zone; excl = 0 is the
+ * paper's rule, which only drops the self-match), for three distances:
+ *
+ *   mp_aamp   pure Euclidean  (Sec. 2, Eq. def-euclidean-distance; Algorithm 1)
+ *   mp_pnorm  p-norm          (Sec. 3.4, Eq. PNormDist1;         Algorithm 3)
+ *   mp_acamp  z-normalised    (Sec. 2, Eq. def-z-normalized;     Algorithm 2)
+ *
+ * The work is the diagonal sweep of Algorithms 1-3: for each diagonal
+ * k = j - i the distance is carried from (i-1, j-1) to (i, j) in O(1)
+ * (Lemmas 1-3) and offered to both P[i] and P[j].
+ *
+ * Conventions shared by every entry point
+ *  - Indices are 0-based.  T holds n samples; P and I hold N = n - m + 1.
+ *  - T, P, I and the workspace are DEVICE pointers owned by the caller.  The
+ *    library never allocates during a call and never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call only enqueues work and returns; results are ready
+ *    when the stream reaches that point.
+ *  - Arguments are validated before anything is enqueued.  On any error the
+ *    call returns a non-zero status, enqueues nothing and leaves P and I
+ *    untouched; mp_last_error() gives a thread-local message.
+ *  - Ties: among equal distances the smallest |i - j| wins, then the left
+ *    neighbour (what the strict '<' of Algorithms 1-3 produces with k and i
+ *    ascending).  With FP32 sweeps, candidates closer than the stated error
+ *    may be ordered either way.
+ *  - Rows with no candidate (N - 1 <= excl) get P = +inf, I = -1.  For the
+ *    z-normalised distance a flat window (centred sum of squares at most
+ *    2^-40 times its raw sum of squares) gets P = +inf, I = -1 and is never a
+ *    neighbour (Sec. 1: its z-normalised distance is undefined).
+ */
+#ifndef MP_H
+#define MP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MP_OK = 0,
+    MP_ERR_INVALID_ARG = 1,  /* bad size, pointer, alignment or option     */
+    MP_ERR_UNSUPPORTED = 2,  /* valid but outside this build's limits      */
+    MP_ERR_WORKSPACE = 3,    /* ws NULL or ws_bytes < mp_workspace_size()  */
+    MP_ERR_CUDA = 4,         /* a CUDA call failed (launch, copy, graph)   */
+    MP_ERR_INTERNAL = 5      /* a device-side check failed                 */
+} mp_status;
+
+typedef enum { MP_F32 = 0, MP_F64 = 1 } mp_dtype;
+
+typedef enum {
+    /* FP32 recurrence re-anchored from exact block sums every `reanchor`
+     * rows; FP64 window statistics; FP64 polish of P at I. */
+    MP_PREC_FP32 = 0,
+    /* FP64 recurrence (slow on this GPU: FP64 runs at 1/64 of FP32). */
+    MP_PREC_FP64 = 1
+} mp_precision;
+
+typedef enum { MP_DIST_EUCLID = 0, MP_DIST_PNORM = 1, MP_DIST_ZNORM = 2 } mp_dist;
+
+typedef struct mp_options {
+    uint32_t struct_size; /* = sizeof(mp_options); set by mp_options_default      */
+    int32_t precision;    /* mp_precision (default MP_PREC_FP32)                  */
+    int32_t reanchor;     /* rows between exact re-anchors; 0 = chosen from m     */
+    int32_t polish;       /* 1 (default): P[i] recomputed in FP64 as d(i, I[i])   */
+                          /* 0: P is the sweep's own (FP32 or FP64) value          */
+    int32_t reserved0;
+    int64_t k_begin;      /* sweep only diagonals k >= k_begin (default 0)        */
+    int64_t k_end;        /* ... and k < k_end (<= 0 means no upper bound).       */
+                          /* Disjoint ranges computed separately and merged with  */
+                          /* the tie rule above give the full profile.            */
+} mp_options;
+
+/* Fill *opt with the defaults.  Passing opt = NULL to any call means the
+ * same thing. */
+void mp_options_default(mp_options *opt);
+
+/* Bytes of device workspace that mp_aamp / mp_pnorm / mp_acamp need for this
+ * problem (dist is an mp_dist, dtype an mp_dtype).  0 on invalid input.
+ * The workspace must be 256-byte aligned. */
+size_t mp_workspace_size(int dist, int dtype, int64_t n, int32_t m, const mp_options *opt);
+
+/* Matrix profile with the pure Euclidean distance (AAMP, Algorithm 1).
+ *   T      device, n samples of type dtype (4- or 8-byte aligned)
+ *   n, m   1 <= m <= n, N = n - m + 1 < 2^31
+ *   excl   >= 0; pairs with |i - j| <= excl are not considered
+ *   P      device, N doubles: the distance to the nearest neighbour
+ *   I      device, N int64: the nearest neighbour's index, or -1
+ *   ws     device workspace of ws_bytes >= mp_workspace_size(MP_DIST_EUCLID, ...)
+ * Errors: MP_ERR_INVALID_ARG (sizes, NULL or misaligned pointers, options),
+ *         MP_ERR_UNSUPPORTED (N >= 2^31), MP_ERR_WORKSPACE, MP_ERR_CUDA. */
+mp_status mp_aamp(const void *T, int dtype, int64_t n, int32_t m, int64_t excl,
+                  double *P, int64_t *I, void *ws, size_t ws_bytes,
+                  const mp_options *opt, void *stream);
+
+/* Matrix profile with the p-norm distance (AAMP for p-norm, Algorithm 3,
+ * Lemma 2), P[i] = (sum_l |t_{i+l} - t_{j+l}|^p)^(1/p).  p >= 1 (real);
+ * p = 1, 2, 3 have specialised kernels, other p use powf.  Other arguments
+ * and errors as mp_aamp. */
+mp_status mp_pnorm(const void *T, int dtype, int64_t n, int32_t m, int64_t excl, double p,
+                   double *P, int64_t *I, void *ws, size_t ws_bytes,
+                   const mp_options *opt, void *stream);
+
+/* Matrix profile with the z-normalised Euclidean distance (ACAMP,
+ * Algorithm 2, Lemma 3).  Window means and centred sums of squares are
+ * computed in FP64; the sweep carries the centred covariance.  m >= 2.
+ * Other arguments and errors as mp_aamp. */
+mp_status mp_acamp(const void *T, int dtype, int64_t n, int32_t m, int64_t excl,
+                   double *P, int64_t *I, void *ws, size_t ws_bytes,
+                   const mp_options *opt, void *stream);
+
+/* Synchronise `stream` and report a sticky CUDA error or a device-side check
+ * failure from earlier calls (MP_ERR_CUDA / MP_ERR_INTERNAL), else MP_OK. */
+mp_status mp_sync_status(void *stream);
+
+/* Thread-local text of the last error (empty string if none). */
+const char *mp_last_error(void);
+
+/* Static name of a status code. */
+const char *mp_status_string(mp_status s);
+
+/* Library version, as "major.minor.patch". */
+const char *mp_version(void);
+
+/* Number of kernels this library has launched in this process so far
+ * (all threads, all devices).  For benchmarks: the difference across a
+ * timed region is the number of the library's kernel launches in it. */
+uint64_t mp_launch_count(void);
+
+/* Profiling hook for the calling host thread.  When both are non-NULL,
+ * every later mp_aamp / mp_pnorm / mp_acamp call on this thread records
+ * `ev_start` (a cudaEvent_t passed as void*) on its stream right before the
+ * diagonal-sweep kernel and `ev_end` right after it, so that the caller can
+ * time the sweep alone with cudaEventElapsedTime.  NULL, NULL turns it off.
+ * The events are owned by the caller.  Always returns MP_OK. */
+mp_status mp_set_sweep_events(void *ev_start, void *ev_end);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MP_H */

@@ -1,0 +1,441 @@
+// C ABI of libmp (declared in include/mp.h): argument checks, workspace
+// layout and the launch sequence of the matrix-profile sweep
+//   a1 convert -> [a2 stats] -> keys init -> a3-a5 sweep -> a6 finalize.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+
+#include "mp.h"
+#include "mp_device.cuh"
+#include "mp_prep.cuh"
+#include "mp_sweep.cuh"
+#include "mp_launch.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+thread_local cudaEvent_t g_ev_start = nullptr, g_ev_end = nullptr;
+std::atomic<unsigned long long> g_launches{0};
+
+// Count one kernel launch of this library (reported by mp_launch_count).
+inline void counted(int n = 1) { g_launches.fetch_add(static_cast<unsigned long long>(n)); }
+
+// Bracket the sweep kernel with the caller's profiling events, if set.
+struct SweepEvents {
+    cudaStream_t st;
+    explicit SweepEvents(cudaStream_t s) : st(s) {
+        if (g_ev_start && g_ev_end) cudaEventRecord(g_ev_start, st);
+    }
+    ~SweepEvents() {
+        if (g_ev_start && g_ev_end) cudaEventRecord(g_ev_end, st);
+    }
+};
+
+mp_status fail(mp_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+mp_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(MP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr size_t ALIGN = 256;
+size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+constexpr int SUM_PARTS = 512;
+
+// Workspace layout of one call.
+struct Layout {
+    size_t keys = 0, keys128 = 0, hi = 0, lo = 0, x64 = 0, part = 0, mean = 0;
+    size_t mu = 0, S = 0, flat = 0, df = 0, dg = 0, inv = 0, muf = 0;
+    size_t total = 0;
+};
+
+struct Problem {
+    int dist;  // mp_dist
+    int dtype;
+    long long n, N;
+    int m;
+    long long excl;
+    double p;
+    mp_options opt;
+    long long k_first, k_end;
+};
+
+Layout layout(const Problem &pb) {
+    Layout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += up(bytes);
+        return o;
+    };
+    const size_t n = pb.n, N = pb.N;
+    const bool f64 = pb.opt.precision == MP_PREC_FP64;
+    if (f64) L.keys128 = take(N * sizeof(mpk::Key128));
+    else L.keys = take(N * sizeof(unsigned long long));
+    if (!f64) {
+        L.hi = take(n * sizeof(float));
+        if (pb.dtype == MP_F64) L.lo = take(n * sizeof(float));
+    }
+    L.x64 = take(n * sizeof(double));
+    L.part = take(SUM_PARTS * sizeof(double));
+    L.mean = take(sizeof(double));
+    if (pb.dist == MP_DIST_ZNORM) {
+        L.mu = take(N * sizeof(double));
+        L.S = take(N * sizeof(double));
+        L.flat = take(N);
+        if (!f64) {
+            L.df = take(N * sizeof(float));
+            L.dg = take(N * sizeof(float));
+            L.inv = take(N * sizeof(float));
+            L.muf = take(N * sizeof(float));
+        }
+    }
+    L.total = off;
+    return L;
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+mp_status check_problem(Problem &pb, const void *T, const double *P, const int64_t *I,
+                        const mp_options *opt) {
+    if (opt) {
+        if (opt->struct_size != sizeof(mp_options))
+            return fail(MP_ERR_INVALID_ARG, "mp_options.struct_size %u != %zu (use mp_options_default)",
+                        opt->struct_size, sizeof(mp_options));
+        pb.opt = *opt;
+    } else {
+        mp_options_default(&pb.opt);
+    }
+    if (pb.dtype != MP_F32 && pb.dtype != MP_F64) return fail(MP_ERR_INVALID_ARG, "dtype %d", pb.dtype);
+    if (pb.n < 1) return fail(MP_ERR_INVALID_ARG, "n = %lld < 1", pb.n);
+    if (pb.m < 1 || pb.m > pb.n) return fail(MP_ERR_INVALID_ARG, "m = %d outside [1, n = %lld]", pb.m, pb.n);
+    if (pb.dist == MP_DIST_ZNORM && pb.m < 2) return fail(MP_ERR_INVALID_ARG, "z-normalised distance needs m >= 2");
+    if (pb.excl < 0) return fail(MP_ERR_INVALID_ARG, "excl = %lld < 0", pb.excl);
+    if (pb.dist == MP_DIST_PNORM && !(pb.p >= 1.0 && std::isfinite(pb.p)))
+        return fail(MP_ERR_INVALID_ARG, "p = %g, need a finite p >= 1", pb.p);
+    if (pb.opt.precision != MP_PREC_FP32 && pb.opt.precision != MP_PREC_FP64)
+        return fail(MP_ERR_INVALID_ARG, "precision %d", pb.opt.precision);
+    if (pb.opt.reanchor < 0) return fail(MP_ERR_INVALID_ARG, "reanchor %d < 0", pb.opt.reanchor);
+    if (pb.opt.polish != 0 && pb.opt.polish != 1) return fail(MP_ERR_INVALID_ARG, "polish %d", pb.opt.polish);
+    if (pb.opt.k_begin < 0) return fail(MP_ERR_INVALID_ARG, "k_begin %lld < 0", (long long)pb.opt.k_begin);
+    if (!T || !P || !I) return fail(MP_ERR_INVALID_ARG, "NULL T, P or I");
+    if (!aligned(T, pb.dtype == MP_F64 ? 8 : 4) || !aligned(P, 8) || !aligned(I, 8))
+        return fail(MP_ERR_INVALID_ARG, "misaligned T, P or I");
+    pb.N = pb.n - pb.m + 1;
+    if (pb.N >= (1ll << 31) - 1) return fail(MP_ERR_UNSUPPORTED, "N = %lld >= 2^31 - 1", pb.N);
+    pb.k_first = std::max<long long>(pb.excl + 1, pb.opt.k_begin);
+    pb.k_end = pb.opt.k_end > 0 ? std::min<long long>(pb.N, pb.opt.k_end) : pb.N;
+    return MP_OK;
+}
+
+// Re-anchor interval B for the FP32 sweep: the largest divisor of m that is at
+// most `target` (default min(64, m / 4): the running score must not drift over
+// more than a quarter of a window) and leaves Q = m / B <= qmax ring blocks.
+void choose_block(int m, int target, int qmax, int &B, int &Q) {
+    if (target <= 0) target = std::max(1, std::min(64, m / 4));
+    int best = 0;
+    for (int b = std::min(m, target); b >= 1; --b)
+        if (m % b == 0 && m / b <= qmax) { best = b; break; }
+    if (best == 0)  // every divisor <= target gives too many blocks: smallest valid one
+        for (int b = (m + qmax - 1) / qmax; b <= m; ++b)
+            if (m % b == 0) { best = b; break; }
+    B = best;
+    Q = m / best;
+}
+
+int grid_for(long long work, int nt) {
+    long long g = (work + nt - 1) / nt;
+    if (g < 1) g = 1;
+    if (g > 65535LL * 16) g = 65535LL * 16;
+    return static_cast<int>(g);
+}
+
+template <typename Tin>
+mp_status prep_series(const Problem &pb, const Layout &L, const void *T, char *ws, cudaStream_t st) {
+    const Tin *t = static_cast<const Tin *>(T);
+    double *x64 = reinterpret_cast<double *>(ws + L.x64);
+    mpk::convert_f64_kernel<Tin><<<grid_for(pb.n, mpk::PREP_NT), mpk::PREP_NT, 0, st>>>(t, pb.n, pb.n, x64);
+    counted();
+    if (pb.opt.precision == MP_PREC_FP32) {
+        const double *shift = nullptr;
+        if (pb.dtype == MP_F64) {
+            double *part = reinterpret_cast<double *>(ws + L.part);
+            double *mean = reinterpret_cast<double *>(ws + L.mean);
+            mpk::sum_partial_kernel<Tin><<<SUM_PARTS, mpk::PREP_NT, 0, st>>>(t, pb.n, part);
+            mpk::sum_final_kernel<<<1, mpk::PREP_NT, 0, st>>>(part, SUM_PARTS, pb.n, mean);
+            counted(2);
+            shift = mean;
+        }
+        mpk::convert_f32_kernel<Tin><<<grid_for(pb.n, mpk::PREP_NT), mpk::PREP_NT, 0, st>>>(
+            t, pb.n, pb.n, shift, reinterpret_cast<float *>(ws + L.hi),
+            L.lo ? reinterpret_cast<float *>(ws + L.lo) : nullptr);
+        counted();
+    }
+    return MP_OK;
+}
+
+template <int KIND, bool SPLIT>
+mp_status launch_sweep_t(const mpk::SweepArgs &a, size_t smem, cudaStream_t st) {
+    auto kern = mpk::sweep_kernel<KIND, SPLIT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(sweep)");
+    {
+        SweepEvents ev(st);
+        kern<<<static_cast<unsigned>(a.tiles), mpk::SW_NT, smem, st>>>(a);
+    }
+    counted();
+    return MP_OK;
+}
+
+mp_status run_sweep_f32(const Problem &pb, const Layout &L, char *ws, cudaStream_t st) {
+    mpk::SweepArgs a{};
+    a.hi = reinterpret_cast<const float *>(ws + L.hi);
+    a.lo = L.lo ? reinterpret_cast<const float *>(ws + L.lo) : nullptr;
+    a.keys = reinterpret_cast<unsigned long long *>(ws + L.keys);
+    a.n = pb.n;
+    a.N = pb.N;
+    a.k_first = pb.k_first;
+    a.k_end = pb.k_end;
+    a.m = pb.m;
+    choose_block(pb.m, pb.opt.reanchor, mpk::SW_QMAX, a.B, a.Q);
+    a.R = 2048;
+    a.q = mpk::SW_KW / a.R;
+    a.RL = mpk::sweep_rows_leaving(a.R, a.m);
+    a.L = pb.N - pb.k_first;
+    a.C = (a.L + a.R - 1) / a.R;
+    const long long nb = (pb.k_end - pb.k_first + mpk::SW_KW - 1) / mpk::SW_KW;
+    a.nb = nb;
+    a.tiles = nb * a.C - static_cast<long long>(a.q) * nb * (nb - 1) / 2;
+    a.p = static_cast<float>(pb.p);
+    if (a.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", a.tiles);
+    const bool split = a.lo != nullptr;
+    const size_t smem = mpk::sweep_smem_bytes(a.R, a.m, a.Q, split);
+    if (smem > 227 * 1024) return fail(MP_ERR_UNSUPPORTED, "m = %d needs %zu bytes of shared memory", pb.m, smem);
+    int kind = mpk::K_P2;
+    if (pb.dist == MP_DIST_PNORM) {
+        kind = pb.p == 2.0 ? mpk::K_P2 : pb.p == 1.0 ? mpk::K_P1 : pb.p == 3.0 ? mpk::K_P3 : mpk::K_PG;
+    }
+    switch (kind * 2 + (split ? 1 : 0)) {
+        case 0: return launch_sweep_t<mpk::K_P2, false>(a, smem, st);
+        case 1: return launch_sweep_t<mpk::K_P2, true>(a, smem, st);
+        case 2: return launch_sweep_t<mpk::K_P1, false>(a, smem, st);
+        case 3: return launch_sweep_t<mpk::K_P1, true>(a, smem, st);
+        case 4: return launch_sweep_t<mpk::K_P3, false>(a, smem, st);
+        case 5: return launch_sweep_t<mpk::K_P3, true>(a, smem, st);
+        case 6: return launch_sweep_t<mpk::K_PG, false>(a, smem, st);
+        default: return launch_sweep_t<mpk::K_PG, true>(a, smem, st);
+    }
+}
+
+mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_t ws_bytes,
+              const mp_options *opt, void *stream) {
+    mp_status s = check_problem(pb, T, P, I, opt);
+    if (s != MP_OK) return s;
+    const Layout L = layout(pb);
+    if (!ws) return fail(MP_ERR_WORKSPACE, "workspace is NULL (need %zu bytes)", L.total);
+    if (!aligned(ws, ALIGN)) return fail(MP_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+    if (ws_bytes < L.total) return fail(MP_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, L.total);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *w = static_cast<char *>(ws);
+    cudaGetLastError();  // clear a stale launch error of an unrelated caller
+
+    const bool f64 = pb.opt.precision == MP_PREC_FP64;
+    s = pb.dtype == MP_F64 ? prep_series<double>(pb, L, T, w, st) : prep_series<float>(pb, L, T, w, st);
+    if (s != MP_OK) return s;
+    if (f64) {
+        mpk::fill_u64_kernel<<<grid_for(2 * pb.N, mpk::PREP_NT), mpk::PREP_NT, 0, st>>>(
+            reinterpret_cast<unsigned long long *>(w + L.keys128), 2 * pb.N, mpk::KEY_NONE);
+        counted();
+    } else {
+        mpk::fill_u64_kernel<<<grid_for(pb.N, mpk::PREP_NT), mpk::PREP_NT, 0, st>>>(
+            reinterpret_cast<unsigned long long *>(w + L.keys), pb.N, mpk::KEY_NONE);
+        counted();
+    }
+    const double *x64 = reinterpret_cast<const double *>(w + L.x64);
+    if (pb.dist == MP_DIST_ZNORM) {
+        mpk::window_stats_kernel<<<grid_for(pb.N, mpk::PREP_NT), mpk::PREP_NT, 0, st>>>(
+            x64, pb.N, pb.m, reinterpret_cast<double *>(w + L.mu), reinterpret_cast<double *>(w + L.S),
+            reinterpret_cast<unsigned char *>(w + L.flat));
+        counted();
+        if (!f64) {
+            mpk::znorm_operands_kernel<<<grid_for(pb.N, mpk::PREP_NT), mpk::PREP_NT, 0, st>>>(
+                x64, pb.N, pb.m, reinterpret_cast<const double *>(w + L.mu),
+                reinterpret_cast<const double *>(w + L.S), reinterpret_cast<const unsigned char *>(w + L.flat),
+                reinterpret_cast<float *>(w + L.df), reinterpret_cast<float *>(w + L.dg),
+                reinterpret_cast<float *>(w + L.inv), reinterpret_cast<float *>(w + L.muf),
+                pb.dtype == MP_F64 ? reinterpret_cast<const double *>(w + L.mean) : nullptr, pb.N);
+            counted();
+        }
+    }
+    if (pb.k_first < pb.k_end) {
+        if (pb.dist == MP_DIST_ZNORM || f64) {
+            const mpk::TileGrid g = mpk::make_grid(pb.N, pb.k_first, pb.k_end, mpk::SM_KW, mpk::SM_KW);
+            if (g.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", g.tiles);
+            int *err = mpk::device_error_ptr();
+            cudaError_t e;
+            SweepEvents ev(st);
+            if (g.tiles > 0) counted();
+            if (pb.dist == MP_DIST_ZNORM && f64) {
+                mpk::VarF64Z v{x64, reinterpret_cast<const double *>(w + L.mu),
+                               reinterpret_cast<const double *>(w + L.S),
+                               reinterpret_cast<const unsigned char *>(w + L.flat), pb.m,
+                               reinterpret_cast<mpk::Key128 *>(w + L.keys128), err};
+                e = mpk::launch_simple(g, v, pb.opt.reanchor > 0 ? pb.opt.reanchor : 256, st);
+            } else if (pb.dist == MP_DIST_ZNORM) {
+                mpk::VarF32Z v{reinterpret_cast<const float *>(w + L.hi), reinterpret_cast<const float *>(w + L.muf),
+                               reinterpret_cast<const float *>(w + L.df), reinterpret_cast<const float *>(w + L.dg),
+                               reinterpret_cast<const float *>(w + L.inv), pb.m,
+                               reinterpret_cast<unsigned long long *>(w + L.keys)};
+                e = mpk::launch_simple(g, v, pb.opt.reanchor > 0 ? pb.opt.reanchor : 512, st);
+            } else {
+                mpk::VarF64Lp v{x64, pb.m, pb.dist == MP_DIST_PNORM ? pb.p : 2.0,
+                                reinterpret_cast<mpk::Key128 *>(w + L.keys128), err};
+                e = mpk::launch_simple(g, v, pb.opt.reanchor > 0 ? pb.opt.reanchor : 256, st);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+        } else {
+            s = run_sweep_f32(pb, L, w, st);
+            if (s != MP_OK) return s;
+        }
+    }
+    mpk::FinalizeArgs fa{};
+    fa.keys = f64 ? nullptr : reinterpret_cast<const unsigned long long *>(w + L.keys);
+    fa.keys128 = f64 ? reinterpret_cast<const mpk::Key128 *>(w + L.keys128) : nullptr;
+    fa.x = x64;
+    fa.mu = L.mu ? reinterpret_cast<const double *>(w + L.mu) : nullptr;
+    fa.S = L.S ? reinterpret_cast<const double *>(w + L.S) : nullptr;
+    fa.N = pb.N;
+    fa.m = pb.m;
+    fa.dist = pb.dist == MP_DIST_EUCLID ? mpk::FIN_EUCLID : pb.dist == MP_DIST_PNORM ? mpk::FIN_PNORM : mpk::FIN_ZNORM;
+    fa.p = pb.dist == MP_DIST_PNORM ? pb.p : 2.0;
+    fa.polish = pb.opt.polish;
+    fa.P = P;
+    fa.I = reinterpret_cast<long long *>(I);
+    mpk::finalize_kernel<<<grid_for(pb.N, mpk::PREP_NT), mpk::PREP_NT, 0, st>>>(fa);
+    counted();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return MP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mp_options_default(mp_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof *opt);
+    opt->struct_size = sizeof(mp_options);
+    opt->precision = MP_PREC_FP32;
+    opt->reanchor = 0;
+    opt->polish = 1;
+    opt->k_begin = 0;
+    opt->k_end = 0;
+}
+
+size_t mp_workspace_size(int dist, int dtype, int64_t n, int32_t m, const mp_options *opt) {
+    Problem pb{};
+    pb.dist = dist;
+    pb.dtype = dtype;
+    pb.n = n;
+    pb.m = m;
+    pb.excl = 0;
+    pb.p = 2.0;
+    if (dist < MP_DIST_EUCLID || dist > MP_DIST_ZNORM) return 0;
+    static const double dummy = 0;
+    if (check_problem(pb, &dummy, reinterpret_cast<const double *>(&dummy),
+                      reinterpret_cast<const int64_t *>(&dummy), opt) != MP_OK)
+        return 0;
+    return layout(pb).total;
+}
+
+mp_status mp_aamp(const void *T, int dtype, int64_t n, int32_t m, int64_t excl, double *P, int64_t *I,
+                  void *ws, size_t ws_bytes, const mp_options *opt, void *stream) {
+    g_err[0] = 0;
+    Problem pb{};
+    pb.dist = MP_DIST_EUCLID;
+    pb.dtype = dtype;
+    pb.n = n;
+    pb.m = m;
+    pb.excl = excl;
+    pb.p = 2.0;
+    return run(pb, T, P, I, ws, ws_bytes, opt, stream);
+}
+
+mp_status mp_pnorm(const void *T, int dtype, int64_t n, int32_t m, int64_t excl, double p, double *P,
+                   int64_t *I, void *ws, size_t ws_bytes, const mp_options *opt, void *stream) {
+    g_err[0] = 0;
+    Problem pb{};
+    pb.dist = MP_DIST_PNORM;
+    pb.dtype = dtype;
+    pb.n = n;
+    pb.m = m;
+    pb.excl = excl;
+    pb.p = p;
+    return run(pb, T, P, I, ws, ws_bytes, opt, stream);
+}
+
+mp_status mp_acamp(const void *T, int dtype, int64_t n, int32_t m, int64_t excl, double *P, int64_t *I,
+                   void *ws, size_t ws_bytes, const mp_options *opt, void *stream) {
+    g_err[0] = 0;
+    Problem pb{};
+    pb.dist = MP_DIST_ZNORM;
+    pb.dtype = dtype;
+    pb.n = n;
+    pb.m = m;
+    pb.excl = excl;
+    pb.p = 2.0;
+    return run(pb, T, P, I, ws, ws_bytes, opt, stream);
+}
+
+mp_status mp_sync_status(void *stream) {
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int err = 0;
+    e = cudaMemcpyFromSymbol(&err, mp_device_error, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+    if (err) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(mp_device_error, &zero, sizeof(int));
+        return fail(MP_ERR_INTERNAL, "device-side check failed (bits 0x%x)", err);
+    }
+    return MP_OK;
+}
+
+const char *mp_last_error(void) { return g_err; }
+
+const char *mp_status_string(mp_status s) {
+    switch (s) {
+        case MP_OK: return "MP_OK";
+        case MP_ERR_INVALID_ARG: return "MP_ERR_INVALID_ARG";
+        case MP_ERR_UNSUPPORTED: return "MP_ERR_UNSUPPORTED";
+        case MP_ERR_WORKSPACE: return "MP_ERR_WORKSPACE";
+        case MP_ERR_CUDA: return "MP_ERR_CUDA";
+        case MP_ERR_INTERNAL: return "MP_ERR_INTERNAL";
+    }
+    return "MP_ERR_UNKNOWN";
+}
+
+const char *mp_version(void) { return "0.1.0"; }
+
+uint64_t mp_launch_count(void) { return g_launches.load(); }
+
+mp_status mp_set_sweep_events(void *ev_start, void *ev_end) {
+    g_ev_start = static_cast<cudaEvent_t>(ev_start);
+    g_ev_end = static_cast<cudaEvent_t>(ev_end);
+    return MP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,251 @@
+// Pre- and post-processing kernels around the diagonal sweep:
+//   a1  convert   series -> FP32 (hi[, lo]) or FP64 copy in the workspace
+//   a2  stats     FP64 window means / centred sums of squares (z-norm)
+//   a6  finalize  keys -> I, P (optionally polished in FP64 at I)
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mp_device.cuh"
+
+namespace mpk {
+
+constexpr int PREP_NT = 256;
+
+// ---- deterministic FP64 sum of the input (two passes, fixed order) -----------
+// Pass 1: block b sums elements b, b + G, b + 2G, ... (grid-stride) into part[b].
+template <typename Tin>
+__global__ void __launch_bounds__(PREP_NT) sum_partial_kernel(const Tin *__restrict__ T, long long n,
+                                                              double *__restrict__ part) {
+    __shared__ double red[PREP_NT];
+    double acc = 0.0;
+    for (long long x = blockIdx.x * (long long)PREP_NT + threadIdx.x; x < n;
+         x += (long long)gridDim.x * PREP_NT)
+        acc += static_cast<double>(T[x]);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = PREP_NT / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// Pass 2: one block adds the partials in a fixed order; out = sum / n.
+__global__ void __launch_bounds__(PREP_NT) sum_final_kernel(const double *__restrict__ part, int nparts,
+                                                            long long n, double *__restrict__ out) {
+    __shared__ double red[PREP_NT];
+    double acc = 0.0;
+    for (int x = threadIdx.x; x < nparts; x += PREP_NT) acc += part[x];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = PREP_NT / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0] / static_cast<double>(n);
+}
+
+// ---- a1: conversion for the FP32 sweep ----------------------------------------
+// FP32 input: hi = t exactly (the differences t_i - t_j the sweep needs are
+// then as exact as FP32 allows); lo = 0.
+// FP64 input: hi + lo represents t - shift to ~2^-48 relative, where shift is
+// the series mean (distances are shift-invariant, Eq. def-euclidean-distance,
+// and z-normalisation removes any offset, Eq. def-z-normalized-distance).
+// Elements in [n, n + pad) are zero so that tile loads may run past the end.
+template <typename Tin>
+__global__ void __launch_bounds__(PREP_NT) convert_f32_kernel(const Tin *__restrict__ T, long long n,
+                                                              long long padded,
+                                                              const double *__restrict__ shift_ptr,
+                                                              float *__restrict__ hi,
+                                                              float *__restrict__ lo) {
+    const double shift = shift_ptr ? shift_ptr[0] : 0.0;
+    for (long long x = blockIdx.x * (long long)PREP_NT + threadIdx.x; x < padded;
+         x += (long long)gridDim.x * PREP_NT) {
+        if (x < n) {
+            const double v = static_cast<double>(T[x]) - shift;
+            const float h = static_cast<float>(v);
+            hi[x] = h;
+            if (lo) lo[x] = static_cast<float>(v - static_cast<double>(h));
+        } else {
+            hi[x] = 0.f;
+            if (lo) lo[x] = 0.f;
+        }
+    }
+}
+
+template <typename Tin>
+__global__ void __launch_bounds__(PREP_NT) convert_f64_kernel(const Tin *__restrict__ T, long long n,
+                                                              long long padded,
+                                                              double *__restrict__ out) {
+    for (long long x = blockIdx.x * (long long)PREP_NT + threadIdx.x; x < padded;
+         x += (long long)gridDim.x * PREP_NT)
+        out[x] = x < n ? static_cast<double>(T[x]) : 0.0;
+}
+
+__global__ void __launch_bounds__(PREP_NT) fill_u64_kernel(unsigned long long *__restrict__ p, long long count,
+                                                           unsigned long long v) {
+    for (long long x = blockIdx.x * (long long)PREP_NT + threadIdx.x; x < count;
+         x += (long long)gridDim.x * PREP_NT)
+        p[x] = v;
+}
+
+// ---- a2: window statistics for the z-normalised distance ----------------------
+// For every window i (Sec. 4.1's A_i and the definition of mu_i, sigma_i):
+//   mu_i  = (1/m) sum_l t_{i+l}
+//   S_i   = sum_l (t_{i+l} - mu_i)^2          (= m sigma_i^2, population)
+//   flat_i: S_i <= 2^-40 sum_l t_{i+l}^2     (sigma = 0 up to rounding)
+// Two passes per window in FP64 over the (shifted) FP64 series x.  One
+// thread per window; neighbouring threads read overlapping windows through
+// the cache.  O(n m) FP64 work, a small share of the sweep for m <= 512.
+__global__ void __launch_bounds__(PREP_NT) window_stats_kernel(const double *__restrict__ x, long long N, int m,
+                                                               double *__restrict__ mu,
+                                                               double *__restrict__ S,
+                                                               unsigned char *__restrict__ flat) {
+    for (long long i = blockIdx.x * (long long)PREP_NT + threadIdx.x; i < N;
+         i += (long long)gridDim.x * PREP_NT) {
+        double a = 0.0;
+        for (int l = 0; l < m; ++l) a += x[i + l];
+        const double mean = a / m;
+        double q = 0.0, r = 0.0;
+        for (int l = 0; l < m; ++l) {
+            const double d = x[i + l] - mean;
+            q = fma(d, d, q);
+            r = fma(x[i + l], x[i + l], r);
+        }
+        mu[i] = mean;
+        S[i] = q;
+        flat[i] = q <= 0x1p-40 * r;
+    }
+}
+
+// FP32 operands of the centred-covariance sweep (derived in FP64):
+//   df_i = (t_{i+m} - t_i) / 2
+//   dg_i = (t_{i+m} - mu_{i+1}) + (t_i - mu_i)
+//   inv_i = 1 / sqrt(S_i)  (NaN for a flat window: every score it touches is NaN
+//                          and never wins a minimum)
+// so that cov_{i+1,j+1} = cov_{i,j} + df_i dg_j + df_j dg_i and
+// rho_{i,j} = cov_{i,j} inv_i inv_j (Lemma 3 with A = m mu, C = cov + m mu_i mu_j).
+__global__ void __launch_bounds__(PREP_NT) znorm_operands_kernel(const double *__restrict__ x, long long N, int m,
+                                                                 const double *__restrict__ mu,
+                                                                 const double *__restrict__ S,
+                                                                 const unsigned char *__restrict__ flat,
+                                                                 float *__restrict__ df, float *__restrict__ dg,
+                                                                 float *__restrict__ inv, float *__restrict__ muf,
+                                                                 const double *__restrict__ shift_ptr,
+                                                                 long long padded) {
+    const double shift = shift_ptr ? shift_ptr[0] : 0.0;  // the offset removed from the FP32 series
+    for (long long i = blockIdx.x * (long long)PREP_NT + threadIdx.x; i < padded;
+         i += (long long)gridDim.x * PREP_NT) {
+        if (i < N) {
+            inv[i] = flat[i] ? __int_as_float(0x7fc00000) : static_cast<float>(1.0 / sqrt(S[i]));
+            muf[i] = static_cast<float>(mu[i] - shift);
+            if (i + 1 < N) {
+                df[i] = static_cast<float>(0.5 * (x[i + m] - x[i]));
+                dg[i] = static_cast<float>((x[i + m] - mu[i + 1]) + (x[i] - mu[i]));
+            } else {
+                df[i] = 0.f;
+                dg[i] = 0.f;
+            }
+        } else {
+            inv[i] = __int_as_float(0x7fc00000);
+            muf[i] = 0.f;
+            df[i] = 0.f;
+            dg[i] = 0.f;
+        }
+    }
+}
+
+// ---- a6: finalize ----------------------------------------------------------------
+enum { FIN_EUCLID = 0, FIN_PNORM = 1, FIN_ZNORM = 2 };
+
+struct FinalizeArgs {
+    const unsigned long long *keys;  // FP32 sweep keys, or
+    const Key128 *keys128;           // FP64 sweep keys
+    const double *x;                 // FP64 series (shifted) for the polish
+    const double *mu, *S;            // z-norm stats (FP64)
+    long long N;
+    int m;
+    int dist;
+    double p;
+    int polish;
+    double *P;
+    long long *I;
+};
+
+__device__ __forceinline__ double pow_abs(double v, double p) {
+    v = fabs(v);
+    if (p == 1.0) return v;
+    if (p == 2.0) return v * v;
+    if (p == 3.0) return v * v * v;
+    return pow(v, p);
+}
+
+// d(i, j) from the definitions (Sec. 2) in FP64.
+__device__ double exact_score(const FinalizeArgs &a, long long i, long long j) {
+    const double *xi = a.x + i, *xj = a.x + j;
+    double acc = 0.0;
+    if (a.dist == FIN_EUCLID) {
+        for (int l = 0; l < a.m; ++l) {
+            const double d = xi[l] - xj[l];
+            acc = fma(d, d, acc);
+        }
+    } else if (a.dist == FIN_PNORM) {
+        for (int l = 0; l < a.m; ++l) acc += pow_abs(xi[l] - xj[l], a.p);
+    } else {
+        const double mi = a.mu[i], mj = a.mu[j];
+        const double si = 1.0 / sqrt(a.S[i] / a.m), sj = 1.0 / sqrt(a.S[j] / a.m);
+        for (int l = 0; l < a.m; ++l) {
+            const double d = (xi[l] - mi) * si - (xj[l] - mj) * sj;
+            acc = fma(d, d, acc);
+        }
+    }
+    return acc;
+}
+
+__device__ __forceinline__ double finish_score(const FinalizeArgs &a, double s) {
+    if (s < 0) s = 0;
+    if (a.dist == FIN_PNORM) {
+        if (a.p == 1.0) return s;
+        if (a.p == 2.0) return sqrt(s);
+        return pow(s, 1.0 / a.p);
+    }
+    return sqrt(s);
+}
+
+__global__ void __launch_bounds__(PREP_NT) finalize_kernel(FinalizeArgs a) {
+    for (long long x = blockIdx.x * (long long)PREP_NT + threadIdx.x; x < a.N;
+         x += (long long)gridDim.x * PREP_NT) {
+        unsigned long long lo;
+        double sweep_score;
+        bool none;
+        if (a.keys) {
+            const unsigned long long key = a.keys[x];
+            none = key == KEY_NONE;
+            lo = key & 0xffffffffull;
+            const float v = __uint_as_float(static_cast<unsigned>(key >> 32));
+            // z-norm keys hold 1 - rho; DZ^2 = 2m(1 - rho) (Lemma 3)
+            sweep_score = a.dist == FIN_ZNORM ? 2.0 * a.m * static_cast<double>(v) : static_cast<double>(v);
+        } else {
+            const Key128 key = a.keys128[x];
+            none = key.hi == KEY_NONE;
+            lo = key.lo;
+            const double v = __longlong_as_double(static_cast<long long>(key.hi));
+            sweep_score = a.dist == FIN_ZNORM ? 2.0 * a.m * v : v;
+        }
+        if (none) {
+            a.P[x] = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+            a.I[x] = -1;
+            continue;
+        }
+        const long long k = static_cast<long long>(lo >> 1);
+        const long long j = (lo & 1) ? x + k : x - k;
+        a.I[x] = j;
+        double s = a.polish ? exact_score(a, x, j) : sweep_score;
+        if (a.dist == FIN_ZNORM) s = fmin(fmax(s, 0.0), 4.0 * a.m);
+        a.P[x] = finish_score(a, s);
+    }
+}
+
+}  // namespace mpk

@@ -1,0 +1,193 @@
+"""Python binding of libmp (include/mp.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; this module only
+turns torch tensors into pointers, owns a cached device workspace, and maps
+status codes to exceptions.  There is no CPU fallback: if the library cannot
+be loaded, every call raises.
+
+    P, I = aamp(T, m, excl)            # pure Euclidean   (Algorithm 1)
+    P, I = pnorm(T, m, excl, p)        # p-norm           (Algorithm 3)
+    P, I = acamp(T, m, excl)           # z-normalised     (Algorithm 2)
+
+T is a 1-D float32/float64 CUDA tensor; P (float64) and I (int64) come back
+on the same device.  Calls are asynchronous on the current torch stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import torch
+
+from . import build as _build
+
+MP_OK, MP_ERR_INVALID_ARG, MP_ERR_UNSUPPORTED, MP_ERR_WORKSPACE, MP_ERR_CUDA, MP_ERR_INTERNAL = range(6)
+MP_F32, MP_F64 = 0, 1
+MP_PREC_FP32, MP_PREC_FP64 = 0, 1
+MP_DIST_EUCLID, MP_DIST_PNORM, MP_DIST_ZNORM = 0, 1, 2
+
+EXPORTS = ("mp_options_default", "mp_workspace_size", "mp_aamp", "mp_pnorm", "mp_acamp",
+           "mp_sync_status", "mp_last_error", "mp_status_string", "mp_version", "mp_launch_count",
+           "mp_set_sweep_events")
+
+
+class MPError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_STATUS = {0: "MP_OK", 1: "MP_ERR_INVALID_ARG", 2: "MP_ERR_UNSUPPORTED", 3: "MP_ERR_WORKSPACE",
+           4: "MP_ERR_CUDA", 5: "MP_ERR_INTERNAL"}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("precision", ctypes.c_int32),
+                ("reanchor", ctypes.c_int32), ("polish", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("k_begin", ctypes.c_int64),
+                ("k_end", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Open libmp.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(path or _build.build())
+        vp, i32, i64, sz, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_double
+        opt_p = ctypes.POINTER(Options)
+        lib.mp_options_default.argtypes = [opt_p]
+        lib.mp_options_default.restype = None
+        lib.mp_workspace_size.argtypes = [ctypes.c_int, ctypes.c_int, i64, i32, opt_p]
+        lib.mp_workspace_size.restype = sz
+        lib.mp_aamp.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, vp, vp, sz, opt_p, vp]
+        lib.mp_aamp.restype = ctypes.c_int
+        lib.mp_pnorm.argtypes = [vp, ctypes.c_int, i64, i32, i64, d, vp, vp, vp, sz, opt_p, vp]
+        lib.mp_pnorm.restype = ctypes.c_int
+        lib.mp_acamp.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, vp, vp, sz, opt_p, vp]
+        lib.mp_acamp.restype = ctypes.c_int
+        lib.mp_sync_status.argtypes = [vp]
+        lib.mp_sync_status.restype = ctypes.c_int
+        lib.mp_last_error.argtypes = []
+        lib.mp_last_error.restype = ctypes.c_char_p
+        lib.mp_status_string.argtypes = [ctypes.c_int]
+        lib.mp_status_string.restype = ctypes.c_char_p
+        lib.mp_version.argtypes = []
+        lib.mp_version.restype = ctypes.c_char_p
+        lib.mp_launch_count.argtypes = []
+        lib.mp_launch_count.restype = ctypes.c_uint64
+        lib.mp_set_sweep_events.argtypes = [vp, vp]
+        lib.mp_set_sweep_events.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def options(precision: str = "fp32", reanchor: int = 0, polish: bool = True,
+            k_range: tuple[int, int] | None = None) -> Options:
+    o = Options()
+    load().mp_options_default(ctypes.byref(o))
+    o.precision = {"fp32": MP_PREC_FP32, "fp64": MP_PREC_FP64}[precision]
+    o.reanchor = int(reanchor)
+    o.polish = 1 if polish else 0
+    if k_range is not None:
+        o.k_begin, o.k_end = int(k_range[0]), int(k_range[1])
+    return o
+
+
+def _check(status: int):
+    if status != MP_OK:
+        raise MPError(status, load().mp_last_error().decode())
+
+
+def workspace_size(dist: int, dtype: int, n: int, m: int, opt: Options | None = None) -> int:
+    return int(load().mp_workspace_size(dist, dtype, n, m, ctypes.byref(opt) if opt else None))
+
+
+_ws_cache: dict = {}
+
+
+def _workspace(device: torch.device, nbytes: int) -> torch.Tensor:
+    """A cached uint8 device buffer of at least nbytes, 256-byte aligned."""
+    key = device.index if device.index is not None else torch.cuda.current_device()
+    buf = _ws_cache.get(key)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
+        _ws_cache[key] = buf
+    return buf
+
+
+def _prep(T: torch.Tensor):
+    if not isinstance(T, torch.Tensor) or not T.is_cuda:
+        raise TypeError("T must be a CUDA tensor (the library has no CPU path)")
+    if T.dim() != 1:
+        raise ValueError("T must be 1-D")
+    if T.dtype not in (torch.float32, torch.float64):
+        raise TypeError("T must be float32 or float64")
+    T = T.contiguous()
+    return T, MP_F32 if T.dtype == torch.float32 else MP_F64
+
+
+def _call(fn_name: str, dist: int, T, m: int, excl: int, p: float | None, opt: Options,
+          out=None, stream=None):
+    lib = load()
+    T, dtype = _prep(T)
+    n = T.numel()
+    N = n - m + 1
+    if out is None:
+        P = torch.empty(max(N, 0), dtype=torch.float64, device=T.device)
+        I = torch.empty(max(N, 0), dtype=torch.int64, device=T.device)
+    else:
+        P, I = out
+    nbytes = lib.mp_workspace_size(dist, dtype, n, m, ctypes.byref(opt))
+    if nbytes == 0:
+        # invalid sizes: let the entry point report the precise error
+        nbytes = 256
+    ws = _workspace(T.device, nbytes)
+    s = stream if stream is not None else torch.cuda.current_stream(T.device)
+    sp = ctypes.c_void_p(s.cuda_stream)
+    args = [ctypes.c_void_p(T.data_ptr()), dtype, n, m, excl]
+    if p is not None:
+        args.append(float(p))
+    args += [ctypes.c_void_p(P.data_ptr()), ctypes.c_void_p(I.data_ptr()),
+             ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.byref(opt), sp]
+    _check(getattr(lib, fn_name)(*args))
+    return P, I
+
+
+def aamp(T, m: int, excl: int, *, precision="fp32", reanchor=0, polish=True, k_range=None,
+         out=None, stream=None):
+    """Matrix profile with the pure Euclidean distance (Algorithm 1)."""
+    return _call("mp_aamp", MP_DIST_EUCLID, T, m, excl, None,
+                 options(precision, reanchor, polish, k_range), out, stream)
+
+
+def pnorm(T, m: int, excl: int, p: float, *, precision="fp32", reanchor=0, polish=True,
+          k_range=None, out=None, stream=None):
+    """Matrix profile with the p-norm distance (Algorithm 3)."""
+    return _call("mp_pnorm", MP_DIST_PNORM, T, m, excl, p,
+                 options(precision, reanchor, polish, k_range), out, stream)
+
+
+def acamp(T, m: int, excl: int, *, precision="fp32", reanchor=0, polish=True, k_range=None,
+          out=None, stream=None):
+    """Matrix profile with the z-normalised Euclidean distance (Algorithm 2)."""
+    return _call("mp_acamp", MP_DIST_ZNORM, T, m, excl, None,
+                 options(precision, reanchor, polish, k_range), out, stream)
+
+
+def sync_status(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(load().mp_sync_status(ctypes.c_void_p(s.cuda_stream)))
+
+
+def profile(T, m, excl, dist="euclid", p=2.0, **kw):
+    if dist in ("euclid", MP_DIST_EUCLID):
+        return aamp(T, m, excl, **kw)
+    if dist in ("pnorm", MP_DIST_PNORM):
+        return pnorm(T, m, excl, p, **kw)
+    return acamp(T, m, excl, **kw)

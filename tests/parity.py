@@ -1,0 +1,77 @@
+"""Parity checks of a GPU matrix profile against the FP64 oracle.
+
+Acceptance (for FP32 sweeps rtol = 1e-5, for FP64 sweeps rtol = 1e-12):
+  (i)   |P - P_ref| <= rtol * P_ref + atol, with the absolute floor
+        atol = rtol * m^(1/p) * sd(diff(T)) (pure / p-norm) or rtol * sqrt(m)
+        (z-norm) that only matters near zero (flat runs, planted copies);
+        the FP32 z-normalised sweep resolves q = 1 - rho = DZ^2 / 2m to an
+        absolute Q_ATOL_Z32 (FP32 rounding of rho), which adds
+        sqrt(P^2 + 2m Q_ATOL_Z32) - P to the tolerance of its rows;
+  (ii)  P[i] equals d(i, I[i]) recomputed by the oracle;
+  (iii) I[i] == I_ref[i] wherever the oracle's runner-up (outside the
+        winner's exclusion zone) is more than the tolerance above the best;
+        elsewhere I[i] must still be a valid neighbour within tolerance.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+Q_ATOL_Z32 = 2e-7
+
+
+def atol_for(T, m, dist, p, rtol):
+    T = np.asarray(T, np.float64)
+    if dist == "znorm":
+        return rtol * np.sqrt(m)
+    sd = np.std(np.diff(T)) if T.size > 1 else 0.0
+    return rtol * m ** (1.0 / p) * max(sd, 1e-300)
+
+
+def check(T, m, excl, dist, p, P, I, rtol, rows=None, P_ref=None, I_ref=None, P2=None,
+          label=""):
+    """Compare (P, I) (numpy, full length N) with the oracle on `rows`
+    (all rows if None).  Reference values may be passed in; otherwise brute
+    force rows are computed here.  Returns a dict of error statistics."""
+    T = np.asarray(T, np.float64)
+    N = T.size - m + 1
+    P = np.asarray(P, np.float64)
+    I = np.asarray(I, np.int64)
+    assert P.shape == (N,) and I.shape == (N,), (P.shape, I.shape, N)
+    rows = np.arange(N) if rows is None else np.asarray(rows, np.int64)
+    if P_ref is None:
+        P_ref, I_ref, P2 = oracle.brute_rows(T, m, excl, rows, dist, p)
+    atol = atol_for(T, m, dist, p, rtol)
+    Pg, Ig = P[rows], I[rows]
+    Pfin = np.where(np.isfinite(P_ref), P_ref, 0.0)
+    tol = rtol * Pfin + atol
+    if dist == "znorm" and rtol >= 1e-6:
+        tol = tol + np.sqrt(Pfin ** 2 + 2 * m * Q_ATOL_Z32) - Pfin
+
+    none = I_ref < 0
+    assert np.all(Ig[none] == -1), f"{label}: rows without candidates got an index"
+    assert np.all(np.isinf(Pg[none])), f"{label}: rows without candidates got a finite P"
+    has = ~none
+    assert np.all(Ig[has] >= 0), f"{label}: {np.sum(Ig[has] < 0)} rows lost their neighbour"
+    # (i)
+    err = np.abs(Pg[has] - P_ref[has])
+    bad = err > tol[has]
+    assert not np.any(bad), (f"{label}: P off in {bad.sum()} rows; worst rel "
+                             f"{np.max(err / np.maximum(P_ref[has], 1e-300)):.3e} at row "
+                             f"{rows[has][np.argmax(err - tol[has])]}")
+    # neighbours must respect the exclusion zone
+    assert np.all(np.abs(Ig[has] - rows[has]) > excl), f"{label}: neighbour inside the exclusion zone"
+    # (ii)
+    d = oracle.pair_dist(T, m, rows[has], Ig[has], dist, p)
+    assert np.all(np.abs(d - Pg[has]) <= tol[has]), f"{label}: P[i] != d(i, I[i])"
+    # (iii)
+    unique = (P2[has] - P_ref[has]) > tol[has]
+    mism = unique & (Ig[has] != I_ref[has])
+    assert not np.any(mism), (f"{label}: I differs in {mism.sum()} rows with a unique winner, e.g. row "
+                              f"{rows[has][np.argmax(mism)]}: got {Ig[has][np.argmax(mism)]}, "
+                              f"want {I_ref[has][np.argmax(mism)]}")
+    assert np.all(d <= P_ref[has] + tol[has]), f"{label}: a non-unique winner is not within tolerance"
+    rel = err / np.maximum(P_ref[has], atol)
+    return {"rows": int(rows.size), "max_rel_err": float(rel.max()) if rel.size else 0.0,
+            "i_mismatch": int(np.sum(Ig[has] != I_ref[has])), "unique": int(unique.sum())}

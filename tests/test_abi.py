@@ -1,0 +1,94 @@
+"""The C ABI library builds, loads and exports what include/mp.h declares; the
+host-side argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1901_05708_gb300 import build as B
+from paper_1901_05708_gb300 import mp
+
+HEADER = os.path.join(B.ROOT, "include", "mp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return mp.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mp_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_function(lib):
+    names = declared_functions()
+    assert "mp_aamp" in names and "mp_acamp" in names and "mp_pnorm" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(mp.EXPORTS) <= set(names)
+
+
+def test_options_and_strings(lib):
+    o = mp.Options()
+    lib.mp_options_default(ctypes.byref(o))
+    assert o.struct_size == ctypes.sizeof(mp.Options)
+    assert o.precision == mp.MP_PREC_FP32 and o.polish == 1 and o.k_end == 0
+    assert lib.mp_status_string(0) == b"MP_OK"
+    assert lib.mp_status_string(3) == b"MP_ERR_WORKSPACE"
+    assert lib.mp_version().count(b".") == 2
+
+
+def test_workspace_size(lib):
+    s1 = lib.mp_workspace_size(mp.MP_DIST_EUCLID, mp.MP_F32, 1 << 20, 256, None)
+    sz = lib.mp_workspace_size(mp.MP_DIST_ZNORM, mp.MP_F32, 1 << 20, 256, None)
+    assert s1 > 8 * (1 << 20) and sz > s1
+    assert s1 % 256 == 0
+    assert lib.mp_workspace_size(mp.MP_DIST_EUCLID, mp.MP_F32, 10, 11, None) == 0
+    assert lib.mp_workspace_size(7, mp.MP_F32, 100, 10, None) == 0
+
+
+def _call_aamp(lib, T=0x1000, dtype=0, n=100, m=10, excl=2, P=0x2000, I=0x3000, ws=0x10000,
+               ws_bytes=1 << 30, opt=None):
+    vp = ctypes.c_void_p
+    return lib.mp_aamp(vp(T), dtype, n, m, excl, vp(P), vp(I), vp(ws), ws_bytes,
+                       ctypes.byref(opt) if opt else None, vp(0))
+
+
+def test_argument_checks_need_no_gpu(lib):
+    """Every rejected call returns before any CUDA call (pointers are fake)."""
+    E = mp
+    assert _call_aamp(lib, m=0) == E.MP_ERR_INVALID_ARG
+    assert _call_aamp(lib, m=101) == E.MP_ERR_INVALID_ARG
+    assert _call_aamp(lib, n=0) == E.MP_ERR_INVALID_ARG
+    assert _call_aamp(lib, excl=-1) == E.MP_ERR_INVALID_ARG
+    assert _call_aamp(lib, dtype=5) == E.MP_ERR_INVALID_ARG
+    assert _call_aamp(lib, T=0) == E.MP_ERR_INVALID_ARG
+    assert _call_aamp(lib, T=0x1002) == E.MP_ERR_INVALID_ARG          # misaligned
+    assert _call_aamp(lib, P=0x2004) == E.MP_ERR_INVALID_ARG
+    assert _call_aamp(lib, ws=0) == E.MP_ERR_WORKSPACE
+    assert _call_aamp(lib, ws_bytes=16) == E.MP_ERR_WORKSPACE
+    assert _call_aamp(lib, ws=0x10010) == E.MP_ERR_INVALID_ARG        # ws not 256-aligned
+    assert _call_aamp(lib, n=1 << 32, m=2) == E.MP_ERR_UNSUPPORTED     # N >= 2^31
+    assert b"m =" in lib.mp_last_error() or lib.mp_last_error() != b""
+    o = mp.Options()
+    lib.mp_options_default(ctypes.byref(o))
+    o.struct_size = 3
+    assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG
+    lib.mp_options_default(ctypes.byref(o))
+    o.precision = 9
+    assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG
+    vp = ctypes.c_void_p
+    assert lib.mp_pnorm(vp(0x1000), 0, 100, 10, 2, 0.5, vp(0x2000), vp(0x3000), vp(0x10000), 1 << 30,
+                        None, vp(0)) == E.MP_ERR_INVALID_ARG
+    assert lib.mp_acamp(vp(0x1000), 0, 100, 1, 2, vp(0x2000), vp(0x3000), vp(0x10000), 1 << 30,
+                        None, vp(0)) == E.MP_ERR_INVALID_ARG
+
+
+def test_binding_refuses_cpu_tensors(lib):
+    torch = pytest.importorskip("torch")
+    with pytest.raises(TypeError):
+        mp.aamp(torch.zeros(100), 10, 2)

@@ -1,0 +1,160 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_05708_gb300 import workloads as W
+
+import parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL32, RTOL64 = 1e-5, 1e-12
+
+
+@pytest.fixture(scope="module")
+def mp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_05708_gb300 import mp as lib
+    lib.load()
+    return lib
+
+
+def run(mp, T, m, excl, dist, p=2.0, **kw):
+    Tt = torch.from_numpy(np.ascontiguousarray(T)).cuda()
+    P, I = mp.profile(Tt, m, excl, dist, p, **kw)
+    torch.cuda.synchronize()
+    mp.sync_status()
+    return P.cpu().numpy(), I.cpu().numpy()
+
+
+DISTS = [("euclid", 2.0), ("pnorm", 1.0), ("pnorm", 3.0), ("pnorm", 2.5), ("znorm", 2.0)]
+
+
+@pytest.mark.parametrize("dist,p", DISTS)
+@pytest.mark.parametrize("n,m,seed", [(40, 3, 0), (300, 8, 1), (700, 32, 2), (2600, 5, 3)])
+def test_small_all_rows(mp, dist, p, n, m, seed):
+    s = W.small("walk", n, m, seed, dtype=np.float32)
+    for excl in (0, s.excl):
+        P, I = run(mp, s.T, m, excl, dist, p)
+        parity.check(s.T, m, excl, dist, p, P, I, RTOL32, label=f"{dist} p={p} n={n} m={m} excl={excl}")
+
+
+@pytest.mark.parametrize("dist,p", DISTS)
+def test_multi_band_ragged(mp, dist, p):
+    """n = 6,000, m = 24: several diagonal bands and row tiles with ragged
+    triangle edges; every row is checked against brute force."""
+    s = W.small("motif", 6000, 24, 11, dtype=np.float32)
+    P, I = run(mp, s.T, s.m, s.excl, dist, p)
+    parity.check(s.T, s.m, s.excl, dist, p, P, I, RTOL32, label=f"{dist} p={p}")
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("dist,p", [("euclid", 2.0), ("pnorm", 1.0), ("pnorm", 3.0)])
+def test_integer_series_bit_exact(mp, seed, dist, p):
+    """Integer data: every FP32 intermediate is an exact integer, so P equals
+    the oracle bit for bit and I follows the paper's tie-break exactly."""
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(100, 5000))
+    m = int(rng.integers(1, 40))
+    T = rng.integers(-8, 9, n).astype(np.float32)
+    for excl in (0, max(1, m // 4)):
+        Pr, Ir = oracle.brute(T, m, excl, dist, p)
+        P, I = run(mp, T, m, excl, dist, p)
+        np.testing.assert_array_equal(I, Ir)
+        if p == 3.0:   # the final cube root is CUDA's pow on one side, libm's on the other
+            np.testing.assert_allclose(P, Pr, rtol=4e-16)
+        else:
+            np.testing.assert_array_equal(P, Pr)
+        P, I = run(mp, T, m, excl, dist, p, polish=False)   # raw sweep value
+        np.testing.assert_array_equal(I, Ir)
+        np.testing.assert_allclose(P, Pr, rtol=1e-6)
+
+
+@pytest.mark.parametrize("dist,p", [("euclid", 2.0), ("pnorm", 3.0), ("znorm", 2.0)])
+def test_fp64_sweep(mp, dist, p):
+    s = W.small("walk", 3000, 20, 21)
+    P, I = run(mp, s.T, s.m, s.excl, dist, p, precision="fp64")
+    parity.check(s.T, s.m, s.excl, dist, p, P, I, RTOL64, label=f"fp64 {dist}")
+    P, I = run(mp, s.T, s.m, s.excl, dist, p, precision="fp64", polish=False)
+    parity.check(s.T, s.m, s.excl, dist, p, P, I, 1e-10, label=f"fp64 raw {dist}")
+
+
+def test_float64_input(mp):
+    """FP64 input on the FP32 path: the hi/lo split keeps differences exact."""
+    s = W.small("walk", 4000, 50, 31)
+    T = s.T * 10.0 + 300.0
+    for dist, p in (("euclid", 2.0), ("pnorm", 1.0), ("znorm", 2.0)):
+        P, I = run(mp, T, s.m, s.excl, dist, p)
+        parity.check(T, s.m, s.excl, dist, p, P, I, RTOL32, label=f"f64 input {dist}")
+
+
+def test_edge_cases(mp):
+    T = W.small("walk", 64, 4, 41, dtype=np.float32).T
+    # no valid pair: N - 1 <= excl
+    P, I = run(mp, T, 4, 61, "euclid")
+    assert np.all(np.isinf(P)) and np.all(I == -1)
+    # m = n: one window
+    P, I = run(mp, T, 64, 0, "euclid")
+    assert P.shape == (1,) and np.isinf(P[0]) and I[0] == -1
+    # m = 1 and excl = 0 (the paper's own exclusion rule)
+    for dist, p in (("euclid", 2.0), ("pnorm", 1.0)):
+        P, I = run(mp, T, 1, 0, dist, p)
+        parity.check(T, 1, 0, dist, p, P, I, RTOL32, label="m=1")
+    # a single valid diagonal
+    P, I = run(mp, T, 4, 59, "euclid")
+    parity.check(T, 4, 59, "euclid", 2.0, P, I, RTOL32, label="one diagonal")
+
+
+def test_flat_run_znorm(mp):
+    s = W.small("flat", 3000, 32, 51, dtype=np.float32)
+    mu, S, flat = oracle.window_stats(s.T, 32)
+    assert flat.sum() > 0
+    P, I = run(mp, s.T, 32, 8, "znorm")
+    assert np.all(np.isinf(P[flat])) and np.all(I[flat] == -1)
+    assert not np.any(flat[I[I >= 0]])
+    parity.check(s.T, 32, 8, "znorm", 2.0, P, I, RTOL32, label="flat z")
+    Pe, Ie = run(mp, s.T, 32, 8, "euclid")
+    parity.check(s.T, 32, 8, "euclid", 2.0, Pe, Ie, RTOL32, label="flat euclid")
+
+
+def test_diagonal_ranges_merge(mp):
+    """Disjoint diagonal ranges merged with the tie rule equal the full run."""
+    T = W.small("int", 5000, 9, 61, dtype=np.float32).T
+    N = T.size - 9 + 1
+    Pf, If = run(mp, T, 9, 2, "euclid")
+    best = np.full(N, np.inf)
+    bkey = np.full(N, np.iinfo(np.int64).max)
+    x = np.arange(N)
+    for r in ((0, 700), (700, 2100), (2100, N)):
+        P, I = run(mp, T, 9, 2, "euclid", k_range=r)
+        key = np.where(I >= 0, 2 * np.abs(I - x) + (I > x), np.iinfo(np.int64).max)
+        take = (P < best) | ((P == best) & (key < bkey))
+        best = np.where(take, P, best)
+        bkey = np.where(take, key, bkey)
+    Irec = np.where(bkey == np.iinfo(np.int64).max, -1, np.where(bkey & 1, x + (bkey >> 1), x - (bkey >> 1)))
+    np.testing.assert_array_equal(best, Pf)
+    np.testing.assert_array_equal(Irec, If)
+
+
+def test_repeatable(mp):
+    s = W.small("walk", 5000, 16, 71, dtype=np.float32)
+    a = run(mp, s.T, s.m, s.excl, "euclid", polish=False)
+    b = run(mp, s.T, s.m, s.excl, "euclid", polish=False)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_invalid_arguments(mp):
+    Tt = torch.zeros(100, device="cuda")
+    with pytest.raises(mp.MPError) as e:
+        mp.aamp(Tt, 101, 0)
+    assert e.value.status == mp.MP_ERR_INVALID_ARG
+    with pytest.raises(mp.MPError):
+        mp.pnorm(Tt, 10, 0, 0.5)
+    with pytest.raises(mp.MPError):
+        mp.aamp(Tt, 10, -1)
+    with pytest.raises(mp.MPError):
+        mp.acamp(Tt, 1, 0)
