@@ -9,12 +9,14 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "mp.h"
 #include "mp_device.cuh"
 #include "mp_prep.cuh"
 #include "mp_sweep.cuh"
+#include "mp_sweep2.cuh"
 #include "mp_launch.cuh"
 
 namespace {
@@ -140,6 +142,13 @@ mp_status check_problem(Problem &pb, const void *T, const double *P, const int64
     return MP_OK;
 }
 
+// MP_FORCE_GENERIC=1 in the environment selects the generic FP32 kernel even
+// where the fast path applies (for comparisons and tests).
+bool getenv_generic() {
+    const char *v = std::getenv("MP_FORCE_GENERIC");
+    return v && v[0] == '1';
+}
+
 // Re-anchor interval B for the FP32 sweep: the largest divisor of m that is at
 // most `target` (default min(64, m / 4): the running score must not drift over
 // more than a quarter of a window) and leaves Q = m / B <= qmax ring blocks.
@@ -199,7 +208,44 @@ mp_status launch_sweep_t(const mpk::SweepArgs &a, size_t smem, cudaStream_t st) 
     return MP_OK;
 }
 
+// Fast Euclidean path (two row streams, f32x2 arithmetic, lazy argmin): FP32
+// input, m a multiple of 32 (re-anchor every m / 4 rows), default re-anchor
+// interval, shared memory for two CTAs per SM.
+bool fast_path_ok(const Problem &pb) {
+    const bool euclid = pb.dist == MP_DIST_EUCLID || (pb.dist == MP_DIST_PNORM && pb.p == 2.0);
+    return euclid && pb.dtype == MP_F32 && pb.m % 32 == 0 && pb.opt.reanchor == 0 &&
+           mpk::sweep2_smem_bytes(pb.m, mpk::V2_QMAX) <= 110 * 1024 && !getenv_generic();
+}
+
+mp_status run_sweep2(const Problem &pb, const Layout &L, char *ws, cudaStream_t st) {
+    mpk::Sweep2Args a{};
+    a.t = reinterpret_cast<const float *>(ws + L.hi);
+    a.keys = reinterpret_cast<unsigned long long *>(ws + L.keys);
+    a.n = pb.n;
+    a.N = pb.N;
+    a.k_first = pb.k_first;
+    a.k_end = pb.k_end;
+    a.m = pb.m;
+    a.Q = mpk::V2_QMAX;  // B = m / 4: a multiple of 8 since m % 32 == 0
+    a.B = pb.m / a.Q;
+    a.L = pb.N - pb.k_first;
+    a.nb = (pb.k_end - pb.k_first + mpk::V2_KW - 1) / mpk::V2_KW;
+    a.tiles = mpk::v2_prefix(a.L, a.nb);
+    if (a.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", a.tiles);
+    if (a.tiles <= 0) return MP_OK;
+    const size_t smem = mpk::sweep2_smem_bytes(a.m, a.Q);
+    cudaError_t e = cudaFuncSetAttribute(mpk::sweep2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(sweep2)");
+    {
+        SweepEvents ev(st);
+        mpk::sweep2_kernel<<<static_cast<unsigned>(a.tiles), mpk::V2_NT, smem, st>>>(a);
+    }
+    counted();
+    return MP_OK;
+}
+
 mp_status run_sweep_f32(const Problem &pb, const Layout &L, char *ws, cudaStream_t st) {
+    if (fast_path_ok(pb)) return run_sweep2(pb, L, ws, st);
     mpk::SweepArgs a{};
     a.hi = reinterpret_cast<const float *>(ws + L.hi);
     a.lo = L.lo ? reinterpret_cast<const float *>(ws + L.lo) : nullptr;

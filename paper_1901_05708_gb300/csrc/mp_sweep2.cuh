@@ -1,0 +1,459 @@
+// a3-a5, fast path: the Euclidean diagonal sweep (Algorithm 1) for FP32
+// series with m a multiple of 32 (re-anchor interval B = m / 4, Q = 4).
+//
+// Same decomposition as the generic kernel (bands of KW diagonals, row
+// tiles, D adjacent diagonals per thread), shaped for the FP32 pipes:
+//
+//  * Two row streams.  A tile of R = 2H rows is walked as two halves at
+//    once: stream a covers rows r0 .. r0+H-1, stream b rows r0+H .. r0+2H-1.
+//    Every diagonal carries one score per stream, held as a float2, so each
+//    arithmetic step is one packed f32x2 instruction for two cells.
+//
+//  * Five packed operations per cell pair.  With e = t_{i+m-1} - t_{j+m-1}
+//    (entering) and f = t_{i-1} - t_{j-1} (leaving), Lemma 1 is carried as
+//        E += e^2,   F' += f^2,   s = E - F'
+//    where, after each exact anchor A, E restarts at 0 and F' at -A; E is
+//    also the sum of the current block of B entering terms that feeds the
+//    ring of exact block sums (see the generic kernel), so the re-anchor
+//    costs nothing per cell.
+//
+//  * Tagged minima.  Each score is tagged with its diagonal slot d in the low
+//    log2(D) mantissa bits (one integer op per cell); tagged scores are still
+//    floats ordered like the scores (to 2^-20 relative), and among equal
+//    scores the smaller d, i.e. the smaller k, is smaller: the paper's
+//    tie-break.  Rows are reduced with 3-input minima over the D slots;
+//    columns (c = i + k) in D rotating slots, two rows at a time with 3-input
+//    minima.  The winner's slot is read back from the tag, so a candidate
+//    that passes its threshold costs two atomics and nothing else.
+//
+//  * Shared memory holds, per tile, the j-side series as float2 pairs
+//    (stream a, stream b) padded by 16 bytes every 64 so that each lane's
+//    16-byte loads hit distinct banks, the i-side pairs, float thresholds
+//    (the best tagged value known for each row / column of the tile; the
+//    column copy padded like the series) and the ring.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mp_device.cuh"
+
+namespace mpk {
+
+constexpr int V2_NT = 128;             // threads per CTA
+constexpr int V2_D = 8;                // diagonals per thread
+constexpr int V2_KW = V2_NT * V2_D;    // diagonals per band
+constexpr int V2_H = 1024;             // rows per stream
+constexpr int V2_R = 2 * V2_H;         // rows per tile
+constexpr int V2_QMAX = 4;             // ring blocks per diagonal
+
+struct Sweep2Args {
+    const float *t;             // FP32 series, n values
+    unsigned long long *keys;   // N profile keys
+    long long n, N;
+    long long k_first, k_end;   // diagonals [k_first, k_end)
+    long long L;                // N - k_first: rows of band 0
+    long long nb;               // bands
+    long long tiles;
+    int m, B, Q;
+};
+
+// ---- f32x2 helpers -----------------------------------------------------------------
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 r;
+    asm("{.reg .b64 ra, rb, rr;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rr, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rr;}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// ---- tile enumeration ---------------------------------------------------------------
+// Band b (diagonals k_first + b KW ...) has L_b = L - b KW rows and
+// ceil(L_b / R) row tiles.  The first tile of band b is
+//   prefix(b) = sum_{b' < b} floor((L - b' KW + R - 1) / R),
+// a floor-sum of an arithmetic progression, evaluated in O(log) steps.
+__host__ __device__ inline long long floor_sum(long long n, long long mdiv, long long a, long long b) {
+    // sum_{i=0}^{n-1} floor((a i + b) / mdiv), a, b >= 0, mdiv > 0
+    long long ans = 0;
+    while (true) {
+        if (a >= mdiv) {
+            ans += (n - 1) * n / 2 * (a / mdiv);
+            a %= mdiv;
+        }
+        if (b >= mdiv) {
+            ans += n * (b / mdiv);
+            b %= mdiv;
+        }
+        const long long y_max = a * n + b;
+        if (y_max < mdiv) break;
+        n = y_max / mdiv;
+        b = y_max % mdiv;
+        const long long t = mdiv;
+        mdiv = a;
+        a = t;
+    }
+    return ans;
+}
+
+__host__ __device__ inline long long v2_prefix(long long L, long long b) {
+    if (b <= 0) return 0;
+    // i = b - 1 - b'  turns the decreasing progression into an increasing one
+    return floor_sum(b, V2_R, V2_KW, L + V2_R - 1 - (b - 1) * V2_KW);
+}
+
+__device__ __forceinline__ bool v2_decode(const Sweep2Args &a, long long t, long long &band, long long &rt) {
+    long long lo = 0, hi = a.nb - 1;  // largest b with prefix(b) <= t
+    while (lo < hi) {
+        const long long mid = (lo + hi + 1) / 2;
+        if (v2_prefix(a.L, mid) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    band = lo;
+    rt = t - v2_prefix(a.L, lo);
+    const long long Lb = a.L - lo * V2_KW;
+    return rt >= 0 && rt * V2_R < Lb;
+}
+
+// padded float2 index of x in the j-side array: 2 pad slots per 8
+__host__ __device__ __forceinline__ int v2_jpos(int x) { return x + 2 * (x >> 3); }
+
+// padded float index of column x in the column-threshold array: 1 pad per 8
+__host__ __device__ __forceinline__ int v2_cpos(int x) { return x + (x >> 3); }
+
+inline size_t sweep2_smem_bytes(int m, int Q) {
+    const size_t nj = v2_jpos(V2_KW + V2_H + m + 16) + 2;
+    const size_t ni = V2_H + m + 16;
+    const size_t nc = v2_cpos(V2_KW + 2 * V2_H + 16);
+    return (nj + ni) * sizeof(float2) + (2 * V2_H + nc) * sizeof(float) +
+           static_cast<size_t>(Q) * V2_D * V2_NT * sizeof(float2);
+}
+
+
+
+// Tag a score with its slot: the low 3 bits of its FP32 pattern become d.
+__device__ __forceinline__ float v2_tag(float s, int d) {
+    return __int_as_float((__float_as_int(s) & ~(V2_D - 1)) | d);
+}
+
+// Threshold form of a value: its bits with all tag bits set, so that a tagged
+// candidate with an equal (masked) value passes "<=" and the global key
+// decides the tie.
+__device__ __forceinline__ float v2_thr_form(unsigned value_bits) { return __uint_as_float(value_bits | (V2_D - 1)); }
+
+// A tagged minimum that passed its threshold: global key + tile threshold.
+__device__ __forceinline__ void v2_emit(unsigned long long *keys, float *thr, int thr_idx, long long target,
+                                        float tagged, long long kt, int right) {
+    const int bits = __float_as_int(tagged);
+    const unsigned v = bits < 0 ? 0u : static_cast<unsigned>(bits & ~(V2_D - 1));
+    atomicMin(&keys[target], make_key(v, kt + (bits & (V2_D - 1)), right));
+    atomicMin(reinterpret_cast<int *>(thr) + thr_idx, static_cast<int>(v | (V2_D - 1)));
+}
+
+// 1 if any of the eight tests a_i <= b_i holds: eight compares chained into
+// one predicate.
+__device__ __forceinline__ int v2_any_le(float a0, float b0, float a1, float b1, float a2, float b2, float a3,
+                                         float b3, float a4, float b4, float a5, float b5, float a6, float b6,
+                                         float a7, float b7) {
+    int r;
+    asm("{ .reg .pred p;\n\t"
+        "setp.le.f32 p, %1, %2;\n\t"
+        "setp.le.or.f32 p, %3, %4, p;\n\t"
+        "setp.le.or.f32 p, %5, %6, p;\n\t"
+        "setp.le.or.f32 p, %7, %8, p;\n\t"
+        "setp.le.or.f32 p, %9, %10, p;\n\t"
+        "setp.le.or.f32 p, %11, %12, p;\n\t"
+        "setp.le.or.f32 p, %13, %14, p;\n\t"
+        "setp.le.or.f32 p, %15, %16, p;\n\t"
+        "selp.s32 %0, 1, 0, p; }"
+        : "=r"(r)
+        : "f"(a0), "f"(b0), "f"(a1), "f"(b1), "f"(a2), "f"(b2), "f"(a3), "f"(b3), "f"(a4), "f"(b4), "f"(a5),
+          "f"(b5), "f"(a6), "f"(b6), "f"(a7), "f"(b7));
+    return r;
+}
+
+__device__ __forceinline__ float v2_min8(const float *t) {
+    return fminf(min3f(t[0], t[1], t[2]), min3f(t[3], t[4], min3f(t[5], t[6], t[7])));
+}
+
+__device__ __forceinline__ float2 v2_sub(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, one rounding
+}
+
+__global__ void __launch_bounds__(V2_NT, 2) sweep2_kernel(const Sweep2Args a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int m = a.m, B = a.B, Q = a.Q;
+    const int tid = threadIdx.x;
+
+    long long band, rt;
+    if (!v2_decode(a, blockIdx.x, band, rt)) {
+        if (tid == 0) atomicOr(&mp_device_error, ERR_BAD_TILE);
+        return;
+    }
+    const long long k0 = a.k_first + band * V2_KW;
+    const long long r0 = rt * V2_R;
+    const long long Lb = a.L - band * V2_KW;  // rows where diagonal k0 is valid
+    const int Rt = static_cast<int>(Lb - r0 < V2_R ? Lb - r0 : V2_R);
+    // rows per stream, a multiple of 8 (stream b's extra rows lie beyond the
+    // band's last row and are masked like any invalid cell)
+    const int Ht = ((Rt + 1) / 2 + V2_D - 1) & ~(V2_D - 1);
+
+    // ---- shared memory
+    //  JT[jpos(x)] = (t[y0 + x], t[y0 + x + Ht]),   y0 = r0 + k0 - 1
+    //  IT[u]       = (t[r0 + u - 1], t[r0 + Ht + u - 1])
+    //  thr_r[u], thr_r[H + u]  threshold of row r0 + u (stream a), r0 + Ht + u (stream b)
+    //  thr_c[cpos(x)]          threshold of column r0 + k0 + x
+    const int njs = v2_jpos(V2_KW + V2_H + m + 16) + 2;
+    float2 *JT = reinterpret_cast<float2 *>(smem);
+    float2 *IT = JT + njs;
+    float *thr_r = reinterpret_cast<float *>(IT + (V2_H + m + 16));
+    float *thr_c = thr_r + 2 * V2_H;
+    float2 *ring = reinterpret_cast<float2 *>(thr_c + v2_cpos(V2_KW + 2 * V2_H + 16));
+
+    const long long y0 = r0 + k0 - 1;
+    auto tv = [&](long long g) -> float { return (g >= 0 && g < a.n) ? a.t[g] : 0.f; };
+    for (int x = tid; x < V2_KW + V2_H + m + 16; x += V2_NT)
+        JT[v2_jpos(x)] = make_float2(tv(y0 + x), tv(y0 + x + Ht));
+    for (int u = tid; u < V2_H + m + 16; u += V2_NT) IT[u] = make_float2(tv(r0 + u - 1), tv(r0 + Ht + u - 1));
+    auto thr_of = [&](long long g) -> float {
+        if (g < 0 || g >= a.N) return 0.f;
+        const unsigned long long key = a.keys[g];
+        return key == KEY_NONE ? __int_as_float(0x7f800000) : v2_thr_form(static_cast<unsigned>(key >> 32));
+    };
+    for (int u = tid; u < V2_H; u += V2_NT) {
+        thr_r[u] = thr_of(r0 + u);
+        thr_r[V2_H + u] = thr_of(r0 + Ht + u);
+    }
+    for (int x = tid; x < V2_KW + 2 * V2_H + 16; x += V2_NT) thr_c[v2_cpos(x)] = thr_of(r0 + k0 + x);
+    __syncthreads();
+
+    const int jb = tid * V2_D;
+    const long long kt = k0 + jb;
+    const long long nd_ll = a.k_end - kt;
+    const int nd = nd_ll <= 0 ? 0 : (nd_ll >= V2_D ? V2_D : static_cast<int>(nd_ll));
+    const long long lim_ll = a.N - kt - r0;  // tile-local row x of slot d is valid iff x + d < lim
+    if (nd == 0 || lim_ll <= 0) return;
+    const int lim = static_cast<int>(lim_ll < 4 * V2_H ? lim_ll : 4 * V2_H);
+    const int lim_b = lim - Ht;  // stream b: stream-local row u valid iff u + d < lim_b
+    const int steps = lim < Ht ? lim : Ht;
+    // rows u < ufast have all 16 cells (both streams, all D slots) valid
+    int ufast = nd == V2_D ? lim_b - (V2_D - 1) : 0;
+    ufast = ufast < 0 ? 0 : (ufast > steps ? steps : ufast);
+    const float NONE = __int_as_float(0x7f800000);  // +inf: above every (finite) tagged score
+
+    // ---- exact anchors at u = 0 from Q block sums (both streams at once)
+    const float4 *JT4 = reinterpret_cast<const float4 *>(JT);
+    float2 s[V2_D], E[V2_D], F[V2_D];
+    // T[r0 + l] = IT[l + 1], T[r0 + k + l] = JT[jb + d + l + 1]; l runs in groups of
+    // 8 so that the j-side window comes in 16-byte loads (jb + l0 is a multiple of 8)
+    for (int qb = 0; qb < Q; ++qb) {
+        float2 beta[V2_D];
+#pragma unroll
+        for (int d = 0; d < V2_D; ++d) beta[d] = make_float2(0.f, 0.f);
+        for (int l0 = qb * B; l0 < qb * B + B; l0 += V2_D) {  // B is a multiple of 8
+            float2 W[2 * V2_D];
+            const int qw = 5 * ((jb + l0) >> 3);
+#pragma unroll
+            for (int q = 0; q < V2_D; ++q) {
+                const float4 w4 = JT4[qw + q + (q >= 4 ? 1 : 0)];
+                W[2 * q] = make_float2(w4.x, w4.y);
+                W[2 * q + 1] = make_float2(w4.z, w4.w);
+            }
+#pragma unroll
+            for (int l = 0; l < V2_D; ++l) {
+                const float2 ti = IT[l0 + l + 1];
+#pragma unroll
+                for (int d = 0; d < V2_D; ++d) {
+                    const float2 e = v2_sub(ti, W[l + d + 1]);
+                    beta[d] = fma2(e, e, beta[d]);
+                }
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < V2_D; ++d) ring[(qb * V2_D + d) * V2_NT + tid] = beta[d];
+    }
+#pragma unroll
+    for (int d = 0; d < V2_D; ++d) {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int qb = 0; qb < Q; ++qb) acc = add2(acc, ring[(qb * V2_D + d) * V2_NT + tid]);
+        s[d] = acc;
+        E[d] = make_float2(0.f, 0.f);
+        F[d] = make_float2(-acc.x, -acc.y);
+    }
+    int anchor_slot = 0;  // ring slot replaced at the next anchor row
+    int next_anchor = B;  // anchor rows are B, 2B, ... (B is a multiple of 8)
+
+    // one step of the recurrence into a row (window offset o = ul + d)
+    auto step = [&](bool anchor, float2 tl, float2 te, const float2 *WL, const float2 *WE, int ul) {
+        if (anchor) {  // re-anchor: the block sum of entering terms just completed
+#pragma unroll
+            for (int d = 0; d < V2_D; ++d) {
+                const float2 e = v2_sub(te, WE[ul + d]);
+                E[d] = fma2(e, e, E[d]);
+                ring[(anchor_slot * V2_D + d) * V2_NT + tid] = E[d];
+                float2 acc = make_float2(0.f, 0.f);
+                for (int qb = 0; qb < Q; ++qb) acc = add2(acc, ring[(qb * V2_D + d) * V2_NT + tid]);
+                s[d] = acc;
+                E[d] = make_float2(0.f, 0.f);
+                F[d] = make_float2(-acc.x, -acc.y);
+            }
+            anchor_slot = anchor_slot + 1 == Q ? 0 : anchor_slot + 1;
+            next_anchor += B;
+        } else {
+#pragma unroll
+            for (int d = 0; d < V2_D; ++d) {
+                const float2 e = v2_sub(te, WE[ul + d]);
+                const float2 f = v2_sub(tl, WL[ul + d]);
+                E[d] = fma2(e, e, E[d]);
+                F[d] = fma2(f, f, F[d]);
+                s[d] = v2_sub(E[d], F[d]);
+            }
+        }
+    };
+    auto row_tgt = [&](int u, int sb) { return r0 + (sb ? Ht : 0) + u; };
+    auto col_tgt = [&](int uc, int sb) { return r0 + (sb ? Ht : 0) + kt + uc; };
+    auto col_idx = [&](int uc, int sb) { return v2_cpos(jb + uc + (sb ? Ht : 0)); };
+
+    // column slots (tagged), per stream; slot (u + d) % D holds column u + d
+    float ca[V2_D], cb[V2_D];
+
+    // masked processing of one row u whose scores are in s; j = u % D must be a
+    // compile-time constant at every call so that the slots stay in registers
+    auto masked_row = [&](int u, int j) {
+        float ta = NONE, tb = NONE;
+#pragma unroll
+        for (int d = 0; d < V2_D; ++d) {
+            const float va = (d < nd && u + d < lim) ? v2_tag(s[d].x, d) : NONE;
+            const float vb = (d < nd && u + d < lim_b) ? v2_tag(s[d].y, d) : NONE;
+            ta = fminf(ta, va);
+            tb = fminf(tb, vb);
+            const int sl = (j + d) % V2_D;
+            ca[sl] = d == V2_D - 1 ? va : fminf(ca[sl], va);
+            cb[sl] = d == V2_D - 1 ? vb : fminf(cb[sl], vb);
+        }
+        if (ta != NONE && ta <= thr_r[u]) v2_emit(a.keys, thr_r, u, row_tgt(u, 0), ta, kt, 1);
+        if (tb != NONE && tb <= thr_r[V2_H + u]) v2_emit(a.keys, thr_r, V2_H + u, row_tgt(u, 1), tb, kt, 1);
+        if (ca[j] != NONE && ca[j] <= thr_c[col_idx(u, 0)]) v2_emit(a.keys, thr_c, col_idx(u, 0), col_tgt(u, 0), ca[j], kt, 0);
+        if (cb[j] != NONE && cb[j] <= thr_c[col_idx(u, 1)]) v2_emit(a.keys, thr_c, col_idx(u, 1), col_tgt(u, 1), cb[j], kt, 0);
+        ca[j] = NONE;
+        cb[j] = NONE;
+    };
+
+    // ---- row 0: the anchors themselves
+#pragma unroll
+    for (int d = 0; d < V2_D; ++d) { ca[d] = NONE; cb[d] = NONE; }
+    masked_row(0, 0);
+
+    // ---- fast region: 8-row blocks (ub, ub + 8] with every cell valid --------------
+    int ub = 0;
+    for (; ub + V2_D < ufast; ub += V2_D) {
+        float2 WL[2 * V2_D], WE[2 * V2_D];
+        {
+            const int qL = 5 * ((jb + ub) >> 3), qE = 5 * ((jb + ub + m) >> 3);
+#pragma unroll
+            for (int q = 0; q < V2_D; ++q) {
+                const int o = q + (q >= 4 ? 1 : 0);
+                const float4 l4 = JT4[qL + o], e4 = JT4[qE + o];
+                WL[2 * q] = make_float2(l4.x, l4.y);
+                WL[2 * q + 1] = make_float2(l4.z, l4.w);
+                WE[2 * q] = make_float2(e4.x, e4.y);
+                WE[2 * q + 1] = make_float2(e4.z, e4.w);
+            }
+        }
+        const bool anc = ub + V2_D == next_anchor;  // B % 8 == 0: anchors fall on a block's last row
+        // per-block bases, so that every access below uses a constant offset
+        const float *tra = thr_r + ub, *trb = thr_r + V2_H + ub;
+        float *tca = thr_c + v2_cpos(jb + ub), *tcb = thr_c + v2_cpos(jb + Ht + ub);  // jb + ub, Ht: multiples of 8
+        const float2 *itl = IT + ub, *ite = IT + ub + m;
+#pragma unroll
+        for (int pr = 0; pr < V2_D / 2; ++pr) {
+            const int ul0 = 2 * pr + 1, ul1 = ul0 + 1;  // rows u0 = ub + ul0, u1 = ub + ul1
+            const int cp0 = ul0 + (ul0 >> 3), cp1 = ul1 + (ul1 >> 3);  // padded column offsets
+            float t0a[V2_D], t0b[V2_D], t1a[V2_D], t1b[V2_D];
+            step(false, itl[ul0], ite[ul0], WL, WE, ul0);
+#pragma unroll
+            for (int d = 0; d < V2_D; ++d) { t0a[d] = v2_tag(s[d].x, d); t0b[d] = v2_tag(s[d].y, d); }
+            step(pr == V2_D / 2 - 1 && anc, itl[ul1], ite[ul1], WL, WE, ul1);
+#pragma unroll
+            for (int d = 0; d < V2_D; ++d) { t1a[d] = v2_tag(s[d].x, d); t1b[d] = v2_tag(s[d].y, d); }
+            const float r0a = v2_min8(t0a), r0b = v2_min8(t0b), r1a = v2_min8(t1a), r1b = v2_min8(t1b);
+            // columns: slot j0 = u0 % D completes column u0, slot j1 completes column u1
+            const int j0 = ul0 % V2_D, j1 = ul1 % V2_D;
+#pragma unroll
+            for (int jj = 0; jj < V2_D; ++jj) {
+                const int sl = (j0 + jj) % V2_D;
+                if (jj == 0) {
+                    ca[sl] = fminf(ca[sl], t0a[0]);
+                    cb[sl] = fminf(cb[sl], t0b[0]);
+                } else if (jj < V2_D - 1) {
+                    ca[sl] = min3f(ca[sl], t0a[jj], t1a[jj - 1]);
+                    cb[sl] = min3f(cb[sl], t0b[jj], t1b[jj - 1]);
+                } else {
+                    ca[sl] = fminf(t0a[jj], t1a[jj - 1]);
+                    cb[sl] = fminf(t0b[jj], t1b[jj - 1]);
+                }
+            }
+            // one test for the 8 candidates of this pair of rows; the rare
+            // pass re-tests each and emits it
+            const int any = v2_any_le(r0a, tra[ul0], r0b, trb[ul0], r1a, tra[ul1], r1b, trb[ul1], ca[j0],
+                                      tca[cp0], cb[j0], tcb[cp0], ca[j1], tca[cp1], cb[j1], tcb[cp1]);
+            if (__builtin_expect(any != 0, 0)) {
+                const int u0 = ub + ul0, u1 = ub + ul1;
+                if (r0a <= tra[ul0]) v2_emit(a.keys, thr_r, u0, row_tgt(u0, 0), r0a, kt, 1);
+                if (r0b <= trb[ul0]) v2_emit(a.keys, thr_r, V2_H + u0, row_tgt(u0, 1), r0b, kt, 1);
+                if (r1a <= tra[ul1]) v2_emit(a.keys, thr_r, u1, row_tgt(u1, 0), r1a, kt, 1);
+                if (r1b <= trb[ul1]) v2_emit(a.keys, thr_r, V2_H + u1, row_tgt(u1, 1), r1b, kt, 1);
+                if (ca[j0] <= tca[cp0]) v2_emit(a.keys, thr_c, col_idx(u0, 0), col_tgt(u0, 0), ca[j0], kt, 0);
+                if (cb[j0] <= tcb[cp0]) v2_emit(a.keys, thr_c, col_idx(u0, 1), col_tgt(u0, 1), cb[j0], kt, 0);
+                if (ca[j1] <= tca[cp1]) v2_emit(a.keys, thr_c, col_idx(u1, 0), col_tgt(u1, 0), ca[j1], kt, 0);
+                if (cb[j1] <= tcb[cp1]) v2_emit(a.keys, thr_c, col_idx(u1, 1), col_tgt(u1, 1), cb[j1], kt, 0);
+            }
+            ca[j0] = t1a[V2_D - 1];
+            cb[j0] = t1b[V2_D - 1];
+            ca[j1] = NONE;
+            cb[j1] = NONE;
+        }
+    }
+
+    // ---- tail: remaining rows, every cell checked (8-row groups keep u % D static)
+    int ulast = ub;
+    for (; ub + 1 < steps; ub += V2_D) {
+#pragma unroll
+        for (int ul = 1; ul <= V2_D; ++ul) {
+            const int u = ub + ul;
+            if (u >= steps) break;
+            float2 WLr[V2_D], WEr[V2_D];
+#pragma unroll
+            for (int d = 0; d < V2_D; ++d) {
+                WLr[d] = JT[v2_jpos(jb + u + d)];
+                WEr[d] = JT[v2_jpos(jb + u + d + m)];
+            }
+            step(u == next_anchor, IT[u], IT[u + m], WLr, WEr, 0);
+            masked_row(u, ul % V2_D);
+            ulast = u;
+        }
+    }
+    // columns still open after the last row: slot sl holds column ulast + ((sl - ulast) mod D)
+#pragma unroll
+    for (int sl = 0; sl < V2_D; ++sl) {
+        const int delta = ((sl - ulast) % V2_D + V2_D) % V2_D;
+        if (delta == 0) continue;
+        const int uc = ulast + delta;
+        if (ca[sl] != NONE && ca[sl] <= thr_c[col_idx(uc, 0)])
+            v2_emit(a.keys, thr_c, col_idx(uc, 0), col_tgt(uc, 0), ca[sl], kt, 0);
+        if (cb[sl] != NONE && cb[sl] <= thr_c[col_idx(uc, 1)])
+            v2_emit(a.keys, thr_c, col_idx(uc, 1), col_tgt(uc, 1), cb[sl], kt, 0);
+    }
+}
+
+}  // namespace mpk

@@ -158,3 +158,32 @@ def test_invalid_arguments(mp):
         mp.aamp(Tt, 10, -1)
     with pytest.raises(mp.MPError):
         mp.acamp(Tt, 1, 0)
+
+
+@pytest.mark.parametrize("m", [32, 64, 96])
+def test_integer_fast_path_bit_exact(mp, m):
+    """The two-stream Euclidean kernel (m a multiple of 8, FP32 input) on
+    integer data: P and I equal the oracle exactly, ties included."""
+    rng = np.random.default_rng(900 + m)
+    T = rng.integers(-8, 9, 7000).astype(np.float32)
+    for excl in (0, m // 4):
+        Pr, Ir = oracle.brute(T, m, excl, "euclid")
+        P, I = run(mp, T, m, excl, "euclid")
+        np.testing.assert_array_equal(I, Ir)
+        np.testing.assert_array_equal(P, Pr)
+
+
+def test_fast_and_generic_kernels_agree(mp, monkeypatch):
+    """Fast and generic FP32 Euclidean kernels against the oracle on a series
+    with many bands and row tiles (n = 40,000, m = 64)."""
+    s = W.small("motif", 40_000, 64, 81, dtype=np.float32)
+    rows = np.random.default_rng(1).choice(s.N, 400, replace=False)
+    ref = oracle.brute_rows(s.T, s.m, s.excl, rows, "euclid")
+    P1, I1 = run(mp, s.T, s.m, s.excl, "euclid")
+    monkeypatch.setenv("MP_FORCE_GENERIC", "1")
+    P2, I2 = run(mp, s.T, s.m, s.excl, "euclid")
+    for P, I, lab in ((P1, I1, "fast"), (P2, I2, "generic")):
+        parity.check(s.T, s.m, s.excl, "euclid", 2.0, P, I, RTOL32, rows=rows,
+                     P_ref=ref[0], I_ref=ref[1], P2=ref[2], label=lab)
+    agree = np.mean(I1 == I2)
+    assert agree > 0.999, agree
