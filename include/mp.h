@@ -145,6 +145,36 @@ uint64_t mp_launch_count(void);
  * The events are owned by the caller.  Always returns MP_OK. */
 mp_status mp_set_sweep_events(void *ev_start, void *ev_end);
 
+/* Size of the library-owned device scratch used by mp_aamp_noalloc. */
+#define MP_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* mp_aamp for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this is a deployment variant.  Some callers
+ * cannot call cudaMalloc or obtain a workspace at all -- a host framework
+ * that owns every device allocation and only hands out input and output
+ * buffers (plugins), or a service that forbids allocation after start-up to
+ * keep its memory budget fixed.  This entry point takes the same arguments
+ * as mp_aamp minus the workspace and instead uses a scratch array of
+ * MP_NOALLOC_SCRATCH_BYTES (32 MiB) that the library declares as static
+ * device memory: every GPU that loads the library holds it until the process
+ * exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ *  - Problems whose workspace (mp_workspace_size(MP_DIST_EUCLID, ...)) is
+ *    larger than the scratch are rejected with MP_ERR_UNSUPPORTED; with
+ *    float32 input that is n up to about 1.6 million samples.
+ *  - The first call on each device looks up the scratch address on that
+ *    device (the device must be current); make that first call before any
+ *    CUDA stream capture.
+ *  - All calls on a device share the one scratch array, which keeps the
+ *    contents of the last call (every call initialises what it reads).
+ *    Calls that overlap on the GPU -- on different streams, or from
+ *    different host threads without ordering -- race on it and give wrong
+ *    results: serialise them.
+ * Results, argument checks and errors are those of mp_aamp. */
+mp_status mp_aamp_noalloc(const void *T, int dtype, int64_t n, int32_t m, int64_t excl,
+                          double *P, int64_t *I, const mp_options *opt, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "mp.h"
 #include "mp_device.cuh"
@@ -378,6 +379,35 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
 
 }  // namespace
 
+// ---- scratch of mp_aamp_noalloc ------------------------------------------------------
+// Static device memory: loaded with the module on every device that uses the
+// library, never allocated or freed by a call.  Host code must not take its
+// address directly (the host symbol is only a stand-in); the device address
+// is looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char mp_noalloc_scratch[MP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+mp_status noalloc_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(MP_ERR_UNSUPPORTED, "device %d", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, mp_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return MP_OK;
+}
+}  // namespace
+
 extern "C" {
 
 void mp_options_default(mp_options *opt) {
@@ -444,6 +474,26 @@ mp_status mp_acamp(const void *T, int dtype, int64_t n, int32_t m, int64_t excl,
     pb.excl = excl;
     pb.p = 2.0;
     return run(pb, T, P, I, ws, ws_bytes, opt, stream);
+}
+
+mp_status mp_aamp_noalloc(const void *T, int dtype, int64_t n, int32_t m, int64_t excl, double *P, int64_t *I,
+                          const mp_options *opt, void *stream) {
+    g_err[0] = 0;
+    const size_t need = mp_workspace_size(MP_DIST_EUCLID, dtype, n, m, opt);
+    if (need > MP_NOALLOC_SCRATCH_BYTES)
+        return fail(MP_ERR_UNSUPPORTED, "n = %lld needs %zu bytes of scratch; mp_aamp_noalloc has %u",
+                    static_cast<long long>(n), need, MP_NOALLOC_SCRATCH_BYTES);
+    void *ws = nullptr;
+    mp_status st = noalloc_scratch(&ws);
+    if (st != MP_OK) return st;
+    Problem pb{};
+    pb.dist = MP_DIST_EUCLID;
+    pb.dtype = dtype;
+    pb.n = n;
+    pb.m = m;
+    pb.excl = excl;
+    pb.p = 2.0;
+    return run(pb, T, P, I, ws, MP_NOALLOC_SCRATCH_BYTES, opt, stream);
 }
 
 mp_status mp_sync_status(void *stream) {
