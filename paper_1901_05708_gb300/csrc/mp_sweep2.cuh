@@ -146,6 +146,18 @@ __device__ __forceinline__ float v2_tag(float s, int d) {
     return __int_as_float((__float_as_int(s) & ~(V2_D - 1)) | d);
 }
 
+// The same for the eight slots of one stream in a single 3-input logic op each:
+// (bits & mask) | d with the mask in a register and d an immediate.
+#define V2_TAG1(i)                                                                      \
+    asm("lop3.b32 %0, %1, %2, " #i ", 0xEA;" : "=r"(o[i]) : "r"(__float_as_int(sb ? s[i].y : s[i].x)), "r"(mask))
+__device__ __forceinline__ void v2_tag8(float *t, const float2 *s, bool sb, int mask) {
+    int o[V2_D];
+    V2_TAG1(0); V2_TAG1(1); V2_TAG1(2); V2_TAG1(3); V2_TAG1(4); V2_TAG1(5); V2_TAG1(6); V2_TAG1(7);
+#pragma unroll
+    for (int d = 0; d < V2_D; ++d) t[d] = __int_as_float(o[d]);
+}
+#undef V2_TAG1
+
 // Threshold form of a value: its bits with all tag bits set, so that a tagged
 // candidate with an equal (masked) value passes "<=" and the global key
 // decides the tie.
@@ -250,6 +262,7 @@ __global__ void __launch_bounds__(V2_NT, 2) sweep2_kernel(const Sweep2Args a) {
     int ufast = nd == V2_D ? lim_b - (V2_D - 1) : 0;
     ufast = ufast < 0 ? 0 : (ufast > steps ? steps : ufast);
     const float NONE = __int_as_float(0x7f800000);  // +inf: above every (finite) tagged score
+    const int tag_mask = ~(V2_D - 1);
 
     // ---- exact anchors at u = 0 from Q block sums (both streams at once)
     const float4 *JT4 = reinterpret_cast<const float4 *>(JT);
@@ -381,11 +394,11 @@ __global__ void __launch_bounds__(V2_NT, 2) sweep2_kernel(const Sweep2Args a) {
             const int cp0 = ul0 + (ul0 >> 3), cp1 = ul1 + (ul1 >> 3);  // padded column offsets
             float t0a[V2_D], t0b[V2_D], t1a[V2_D], t1b[V2_D];
             step(false, itl[ul0], ite[ul0], WL, WE, ul0);
-#pragma unroll
-            for (int d = 0; d < V2_D; ++d) { t0a[d] = v2_tag(s[d].x, d); t0b[d] = v2_tag(s[d].y, d); }
+            v2_tag8(t0a, s, false, tag_mask);
+            v2_tag8(t0b, s, true, tag_mask);
             step(pr == V2_D / 2 - 1 && anc, itl[ul1], ite[ul1], WL, WE, ul1);
-#pragma unroll
-            for (int d = 0; d < V2_D; ++d) { t1a[d] = v2_tag(s[d].x, d); t1b[d] = v2_tag(s[d].y, d); }
+            v2_tag8(t1a, s, false, tag_mask);
+            v2_tag8(t1b, s, true, tag_mask);
             const float r0a = v2_min8(t0a), r0b = v2_min8(t0b), r1a = v2_min8(t1a), r1b = v2_min8(t1b);
             // columns: slot j0 = u0 % D completes column u0, slot j1 completes column u1
             const int j0 = ul0 % V2_D, j1 = ul1 % V2_D;
