@@ -162,10 +162,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(series: W.Series) -> dict:
-    return {"workload": f"{series.name} (AAMP pure Euclidean, float32 random walk + 20 Gaussian bumps)",
+WORKLOADS = {
+    # name: (series factory, description, FP32-pipe instructions per cell at minimum)
+    "aamp_1m": (lambda seed, n: W.aamp_1m(seed=seed, n=n),
+                "AAMP pure Euclidean, float32 random walk + 20 Gaussian bumps", 4),
+    "acamp_1m": (lambda seed, n: W.acamp_1m(seed=seed + 2, n=n),
+                 "ACAMP z-normalised, float32 random walk + N(0, 0.01)", 4),
+    "pnorm_p1": (lambda seed, n: W.pnorm_262k(1.0, seed=seed + 1, n=min(n, 1 << 18)),
+                 "p-norm p = 1, float32 sine + motifs + flat run", 4),
+    "pnorm_p3": (lambda seed, n: W.pnorm_262k(3.0, seed=seed + 1, n=min(n, 1 << 18)),
+                 "p-norm p = 3, float32 sine + motifs + flat run", 6),
+    "aamp_small": (lambda seed, n: W.aamp_small(seed=seed - 1),
+                   "AAMP pure Euclidean, float64 random walk, n = 10,000", 4),
+}
+
+
+def workload_config(series: W.Series, desc: str = WORKLOADS["aamp_1m"][1], precision: str = "fp32") -> dict:
+    prec = ("fp32 sweep (re-anchored / compensated), fp64 polish" if precision == "fp32"
+            else "fp64 sweep, fp64 polish")
+    return {"workload": f"{series.name} ({desc})",
             "n": series.n, "m": series.m, "excl": series.excl, "N": series.N,
-            "cells_per_step": series.cells, "precision": "fp32 sweep re-anchored every 64 rows, fp64 polish",
+            "cells_per_step": series.cells, "precision": prec,
             "l2": "flushed before every timed step (512 MiB write)"}
 
 
@@ -179,6 +196,12 @@ def main():
     ap.add_argument("--warmup-ref", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--workload", default="aamp_1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--k-range", type=int, nargs=2, default=None,
+                    help="sweep only diagonals [k0, k1) (for timing the FP64 sweep on a slice)")
+    ap.add_argument("--fp64-diagonals", type=int, default=8192,
+                    help="also time the FP64 sweep on this many diagonals (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -194,7 +217,9 @@ def main():
     dev = torch.device("cuda", local)
     lib = mp.load()
 
-    series = W.aamp_1m(seed=1 + rank, n=args.n)
+    make, desc, instr_per_cell = WORKLOADS[args.workload]
+    series = make(1 + rank, args.n)
+    dist = {W.EUCLID: "euclid", W.PNORM: "pnorm", W.ZNORM: "znorm"}[series.dist]
     T_host = torch.from_numpy(series.T).pin_memory()
     T = T_host.to(dev)
     N = series.N
@@ -203,8 +228,12 @@ def main():
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
+    kw = {"precision": args.precision}
+    if args.k_range:
+        kw["k_range"] = tuple(args.k_range)
+
     def step():
-        mp.aamp(T, series.m, series.excl, out=(P, I))
+        mp.profile(T, series.m, series.excl, dist, series.p, out=(P, I), **kw)
 
     for _ in range(args.warmup):
         step()
@@ -246,6 +275,9 @@ def main():
         dist.barrier()
 
     cells = series.cells
+    if args.k_range:
+        lo, hi = max(args.k_range[0], series.excl + 1), min(args.k_range[1], series.N)
+        cells = sum(series.N - k for k in range(lo, hi))
     value = ws * cells * args.steps / (total_ms * 1e-3) / 1e9
 
     # ---- end to end through the public API with host buffers -------------------
@@ -258,7 +290,7 @@ def main():
     e0.record(stream)
     for _ in range(e2e_steps):
         T_dev2.copy_(T_host, non_blocking=True)
-        mp.aamp(T_dev2, series.m, series.excl, out=(P, I))
+        mp.profile(T_dev2, series.m, series.excl, dist, series.p, out=(P, I), **kw)
         P_host.copy_(P, non_blocking=True)
         I_host.copy_(I, non_blocking=True)
     e1.record(stream)
@@ -266,34 +298,62 @@ def main():
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
     e2e_value = ws * cells / (e2e_ms * 1e-3) / 1e9
 
+    # ---- the FP64 sweep on a slice of the same diagonals (kernel events only) ----------
+    fp64 = None
+    if args.precision == "fp32" and not args.k_range and args.fp64_diagonals > 0:
+        k0 = series.excl + 1
+        k1 = min(series.N, k0 + args.fp64_diagonals)
+        kw64 = {"precision": "fp64", "k_range": (k0, k1)}
+        mp.profile(T, series.m, series.excl, dist, series.p, out=(P, I), **kw64)  # warm-up
+        ms64 = []
+        for k in range(2):
+            flush.fill_(k & 0xff)
+            lib.mp_set_sweep_events(ctypes_event(sw[k][0]), ctypes_event(sw[k][1]))
+            mp.profile(T, series.m, series.excl, dist, series.p, out=(P, I), **kw64)
+            lib.mp_set_sweep_events(None, None)
+            torch.cuda.synchronize()
+            ms64.append(sw[k][0].elapsed_time(sw[k][1]))
+        mp.sync_status()
+        cells64 = sum(series.N - k for k in range(k0, k1))
+        g64 = cells64 / (float(np.mean(ms64)) * 1e-3) / 1e9
+        fp64 = {"value": g64, "unit": UNIT, "diagonals": [k0, k1], "cells": cells64,
+                "kernel_ms": float(np.mean(ms64)),
+                "what": "FP64 sweep kernel alone (no re-anchoring needed), same series, first diagonals"}
+
     # ---- roofline of the dominant kernel (the diagonal sweep) ------------------------
     pk, src = peaks()
     f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_cells = sms * FP32_LANES_PER_SM * f_max / FP32_INSTR_PER_CELL / 1e9
+    peak_cells = sms * FP32_LANES_PER_SM * f_max / instr_per_cell / 1e9
     sweep_avg_ms = float(np.mean(sweep_ms))
     achieved = cells / (sweep_avg_ms * 1e-3) / 1e9
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_cells, "unit": UNIT,
             "frac": achieved / peak_cells, "traffic": None,
             "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {f_max/1e6:.0f} MHz "
-                           f"({src} sm_max_mhz) / {FP32_INSTR_PER_CELL} FP32 instructions per cell",
-            "kernel": "mpk::sweep_kernel<K_P2,false>", "kernel_ms": sweep_avg_ms}
+                           f"({src} sm_max_mhz) / {instr_per_cell} FP32 instructions per cell",
+            "kernel": "diagonal sweep (a3-a5)", "kernel_ms": sweep_avg_ms}
     if clk.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (sms * FP32_LANES_PER_SM * clk["sm_mhz"] * 1e6
-                                                     / FP32_INSTR_PER_CELL / 1e9)
+                                                     / instr_per_cell / 1e9)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(series), "roofline": roof, "clocks": clk,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic", "config": workload_config(series, desc, args.precision), "roofline": roof,
+            "clocks": clk,
             "gpu_launches": int(launches),
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(T_host.numel() * 4),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(T_host.numel() * T_host.element_size()),
                     "d2h_bytes_per_step": int(N * 16), "ms_per_step": e2e_ms}}
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if args.k_range:
+        line["config"]["k_range"] = list(args.k_range)
+    if fp64 is not None:
+        fp64["fp32_over_fp64"] = achieved / fp64["value"]
+        line["fp64_sweep"] = fp64
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and series.dist == W.EUCLID:
         cb = oracle_sample(series, target_s=args.ref_seconds)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
     elif rank == 0:
-        line["cpu_baseline"] = None
+        line["cpu_baseline"] = None  # the CPU baseline is timed on the default Euclidean workload
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

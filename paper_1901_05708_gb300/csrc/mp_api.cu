@@ -18,6 +18,7 @@
 #include "mp_prep.cuh"
 #include "mp_sweep.cuh"
 #include "mp_sweep2.cuh"
+#include "mp_sweep_z2.cuh"
 #include "mp_launch.cuh"
 
 namespace {
@@ -60,7 +61,7 @@ constexpr int SUM_PARTS = 512;
 // Workspace layout of one call.
 struct Layout {
     size_t keys = 0, keys128 = 0, hi = 0, lo = 0, x64 = 0, part = 0, mean = 0;
-    size_t mu = 0, S = 0, flat = 0, df = 0, dg = 0, inv = 0, muf = 0;
+    size_t mu = 0, S = 0, flat = 0, df = 0, dg = 0, inv = 0, muf = 0, mul = 0;
     size_t total = 0;
 };
 
@@ -103,6 +104,7 @@ Layout layout(const Problem &pb) {
             L.dg = take(N * sizeof(float));
             L.inv = take(N * sizeof(float));
             L.muf = take(N * sizeof(float));
+            L.mul = take(N * sizeof(float));
         }
     }
     L.total = off;
@@ -322,6 +324,7 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
                 reinterpret_cast<const double *>(w + L.S), reinterpret_cast<const unsigned char *>(w + L.flat),
                 reinterpret_cast<float *>(w + L.df), reinterpret_cast<float *>(w + L.dg),
                 reinterpret_cast<float *>(w + L.inv), reinterpret_cast<float *>(w + L.muf),
+                reinterpret_cast<float *>(w + L.mul),
                 pb.dtype == MP_F64 ? reinterpret_cast<const double *>(w + L.mean) : nullptr, pb.N);
             counted();
         }
@@ -340,6 +343,31 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
                                reinterpret_cast<const unsigned char *>(w + L.flat), pb.m,
                                reinterpret_cast<mpk::Key128 *>(w + L.keys128), err};
                 e = mpk::launch_simple(g, v, pb.opt.reanchor > 0 ? pb.opt.reanchor : 256, st);
+            } else if (pb.dist == MP_DIST_ZNORM && !getenv_generic()) {
+                mpk::SweepZArgs za{};
+                za.t = reinterpret_cast<const float *>(w + L.hi);
+                za.tlo = pb.dtype == MP_F64 ? reinterpret_cast<const float *>(w + L.lo) : nullptr;
+                za.muh = reinterpret_cast<const float *>(w + L.muf);
+                za.mul = reinterpret_cast<const float *>(w + L.mul);
+                za.df = reinterpret_cast<const float *>(w + L.df);
+                za.dg = reinterpret_cast<const float *>(w + L.dg);
+                za.inv = reinterpret_cast<const float *>(w + L.inv);
+                za.keys = reinterpret_cast<unsigned long long *>(w + L.keys);
+                za.n = pb.n;
+                za.N = pb.N;
+                za.k_first = pb.k_first;
+                za.k_end = pb.k_end;
+                za.m = pb.m;
+                za.L = pb.N - pb.k_first;
+                za.nb = (pb.k_end - pb.k_first + mpk::Z_KW - 1) / mpk::Z_KW;
+                za.tiles = mpk::z_prefix(za.L, za.nb);
+                if (za.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", za.tiles);
+                const size_t smem = mpk::sweepz_smem_bytes();
+                e = cudaFuncSetAttribute(mpk::sweepz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e == cudaSuccess && za.tiles > 0) {
+                    mpk::sweepz_kernel<<<static_cast<unsigned>(za.tiles), mpk::Z_NT, smem, st>>>(za);
+                    e = cudaGetLastError();
+                }
             } else if (pb.dist == MP_DIST_ZNORM) {
                 mpk::VarF32Z v{reinterpret_cast<const float *>(w + L.hi), reinterpret_cast<const float *>(w + L.muf),
                                reinterpret_cast<const float *>(w + L.df), reinterpret_cast<const float *>(w + L.dg),

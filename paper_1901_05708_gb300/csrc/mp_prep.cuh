@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(PREP_NT) znorm_operands_kernel(const double *_
                                                                  const unsigned char *__restrict__ flat,
                                                                  float *__restrict__ df, float *__restrict__ dg,
                                                                  float *__restrict__ inv, float *__restrict__ muf,
+                                                                 float *__restrict__ mul,
                                                                  const double *__restrict__ shift_ptr,
                                                                  long long padded) {
     const double shift = shift_ptr ? shift_ptr[0] : 0.0;  // the offset removed from the FP32 series
@@ -140,7 +141,9 @@ __global__ void __launch_bounds__(PREP_NT) znorm_operands_kernel(const double *_
          i += (long long)gridDim.x * PREP_NT) {
         if (i < N) {
             inv[i] = flat[i] ? __int_as_float(0x7fc00000) : static_cast<float>(1.0 / sqrt(S[i]));
-            muf[i] = static_cast<float>(mu[i] - shift);
+            const double ms = mu[i] - shift;
+            muf[i] = static_cast<float>(ms);
+            if (mul) mul[i] = static_cast<float>(ms - static_cast<double>(muf[i]));  // float-float mean
             if (i + 1 < N) {
                 df[i] = static_cast<float>(0.5 * (x[i + m] - x[i]));
                 dg[i] = static_cast<float>((x[i + m] - mu[i + 1]) + (x[i] - mu[i]));
@@ -151,6 +154,7 @@ __global__ void __launch_bounds__(PREP_NT) znorm_operands_kernel(const double *_
         } else {
             inv[i] = __int_as_float(0x7fc00000);
             muf[i] = 0.f;
+            if (mul) mul[i] = 0.f;
             df[i] = 0.f;
             dg[i] = 0.f;
         }

@@ -1,0 +1,360 @@
+// a3-a5 for the z-normalised distance (Algorithm 2): the fast FP32 sweep.
+//
+// The sweep carries, per diagonal, the centred covariance
+//   cov_{i,j} = sum_l (t_{i+l} - mu_i)(t_{j+l} - mu_j)
+// with the O(1) update cov_{i,j} = cov_{i-1,j-1} + df_{i-1} dg_{j-1} + df_{j-1} dg_{i-1}
+// (Lemma 3's sums rewritten around the window means; df, dg, inv = 1/sqrt(S)
+// come from the FP64 statistics kernel) and scores each cell with
+//   q = 1 - rho = 1 - cov inv_i inv_j          (DZ^2 = 2 m q, Lemma 3).
+// FP32 cannot hold cov to the 1e-9 relative that q ~ 0.01 needs over tens of
+// thousands of steps, so cov is a float-float pair (hi, lo) updated with an
+// error-free Fast2Sum: 9 packed f32x2 operations per cell pair.
+//
+// Tiles are tall (a band of KW diagonals by up to S rows, split into two row
+// streams packed in f32x2 as in the Euclidean fast path), so the anchor of
+// each stream -- the covariance summed from the definition in float-float --
+// is paid once per S/2 rows.  The tile is walked in chunks of RC rows per
+// stream; each chunk's operands (j side: df, dg, inv of the partner windows;
+// i side: df, dg, inv of the rows) and the current best values of its rows
+// and columns are staged in shared memory, and the chunk's threads read them
+// with conflict-free 16-byte loads.  Minima are tagged exactly as in the
+// Euclidean fast path.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mp_device.cuh"
+#include "mp_sweep2.cuh"
+
+namespace mpk {
+
+constexpr int Z_NT = 128;             // threads per CTA
+constexpr int Z_D = 8;                // diagonals per thread
+constexpr int Z_KW = Z_NT * Z_D;      // diagonals per band
+constexpr int Z_HS = 4096;            // rows per stream per tile (at most)
+constexpr int Z_S = 2 * Z_HS;         // rows per tile
+constexpr int Z_RC = 256;             // rows per stream per chunk
+
+struct SweepZArgs {
+    const float *t;                   // FP32 series (shifted like the means)
+    const float *tlo;                 // low parts of a float64 series (t + tlo), or null
+    const float *muh, *mul;           // window means as float-float (shifted)
+    const float *df, *dg, *inv;       // operands (inv = NaN for a flat window)
+    unsigned long long *keys;
+    long long n, N, k_first, k_end, L, nb, tiles;
+    int m;
+};
+
+__host__ __device__ inline long long z_prefix(long long L, long long b) {
+    if (b <= 0) return 0;
+    return floor_sum(b, Z_S, Z_KW, L + Z_S - 1 - (b - 1) * Z_KW);
+}
+
+__device__ __forceinline__ bool z_decode(const SweepZArgs &a, long long t, long long &band, long long &rt) {
+    long long lo = 0, hi = a.nb - 1;
+    while (lo < hi) {
+        const long long mid = (lo + hi + 1) / 2;
+        if (z_prefix(a.L, mid) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    band = lo;
+    rt = t - z_prefix(a.L, lo);
+    const long long Lb = a.L - lo * Z_KW;
+    return rt >= 0 && rt * Z_S < Lb;
+}
+
+inline size_t sweepz_smem_bytes() {
+    const size_t nj = v2_jpos(Z_KW + Z_RC + 16) + 2;  // per j-side array
+    const size_t ni = Z_RC + 16;                       // per i-side array
+    const size_t nc = v2_cpos(Z_KW + Z_RC + 16);       // column thresholds, per stream
+    return 3 * (nj + ni) * sizeof(float2) + (2 * (Z_RC + 8) + 2 * nc) * sizeof(float);
+}
+
+__device__ __forceinline__ float2 z_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+__global__ void __launch_bounds__(Z_NT, 2) sweepz_kernel(const SweepZArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int m = a.m;
+    const int tid = threadIdx.x;
+
+    long long band, rt;
+    if (!z_decode(a, blockIdx.x, band, rt)) {
+        if (tid == 0) atomicOr(&mp_device_error, ERR_BAD_TILE);
+        return;
+    }
+    const long long k0 = a.k_first + band * Z_KW;
+    const long long r0 = rt * Z_S;
+    const long long Lb = a.L - band * Z_KW;
+    const int Rt = static_cast<int>(Lb - r0 < Z_S ? Lb - r0 : Z_S);
+    const int Hs = ((Rt + 1) / 2 + Z_D - 1) & ~(Z_D - 1);  // rows per stream, a multiple of 8
+    const long long rb = r0 + Hs;                           // first row of stream b
+
+    const int njs = v2_jpos(Z_KW + Z_RC + 16) + 2;
+    float2 *JF = reinterpret_cast<float2 *>(smem);
+    float2 *JG = JF + njs;
+    float2 *JI = JG + njs;
+    float2 *IF = JI + njs;
+    float2 *IG = IF + (Z_RC + 16);
+    float2 *II = IG + (Z_RC + 16);
+    float *thr_r = reinterpret_cast<float *>(II + (Z_RC + 16));  // [2 (RC + 8)]: stream a rows, stream b rows
+    const int ncs = v2_cpos(Z_KW + Z_RC + 16);
+    float *thr_ca = thr_r + 2 * (Z_RC + 8);
+    float *thr_cb = thr_ca + ncs;
+
+    const int jb = tid * Z_D;
+    const long long kt = k0 + jb;
+    const long long nd_ll = a.k_end - kt;
+    const int nd = nd_ll <= 0 ? 0 : (nd_ll >= Z_D ? Z_D : static_cast<int>(nd_ll));
+    const long long lim_ll = a.N - kt - r0;  // tile-local row x of slot d valid iff x + d < lim
+    const bool active = nd > 0 && lim_ll > 0;
+    const int lim = static_cast<int>(lim_ll <= 0 ? 0 : (lim_ll < 4 * Z_HS ? lim_ll : 4 * Z_HS));
+    const int lim_b = lim - Hs;
+    const int steps = lim < Hs ? lim : Hs;  // stream-local rows this thread walks
+    int ufast = nd == Z_D ? lim_b - (Z_D - 1) : 0;
+    ufast = ufast < 0 ? 0 : (ufast > steps ? steps : ufast);
+    const float NONE = __int_as_float(0x7f800000);
+    const float THR_OPEN = __int_as_float(0x7f7fffff);  // largest finite float
+    const int tag_mask = ~(Z_D - 1);
+    const float2 ONE = make_float2(1.f, 1.f);
+
+    // ---- anchors: cov of (row r_s, diagonal kt + d) in float-float, from the definition
+    float2 ch[Z_D], cl[Z_D];  // negated covariance, hi and lo
+    if (active) {
+        auto tv = [&](long long g) -> float { return (g >= 0 && g < a.n) ? __ldg(a.t + g) : 0.f; };
+        auto tl = [&](long long g) -> float { return (a.tlo && g >= 0 && g < a.n) ? __ldg(a.tlo + g) : 0.f; };
+        auto mv = [&](const float *p, long long g) -> float { return (g >= 0 && g < a.N) ? __ldg(p + g) : 0.f; };
+        const float2 mih = make_float2(mv(a.muh, r0), mv(a.muh, rb)), mil = make_float2(mv(a.mul, r0), mv(a.mul, rb));
+        float2 mjh[Z_D], mjl[Z_D];
+#pragma unroll
+        for (int d = 0; d < Z_D; ++d) {
+            mjh[d] = make_float2(mv(a.muh, r0 + kt + d), mv(a.muh, rb + kt + d));
+            mjl[d] = make_float2(mv(a.mul, r0 + kt + d), mv(a.mul, rb + kt + d));
+            ch[d] = make_float2(0.f, 0.f);
+            cl[d] = make_float2(0.f, 0.f);
+        }
+        for (int l = 0; l < m; ++l) {
+            const float2 ti = make_float2(tv(r0 + l), tv(rb + l));
+            const float2 til = make_float2(tl(r0 + l), tl(rb + l));
+            const float2 ci = add2(v2_sub(ti, mih), v2_sub(til, mil));
+#pragma unroll
+            for (int d = 0; d < Z_D; ++d) {
+                const float2 tj = make_float2(tv(r0 + kt + d + l), tv(rb + kt + d + l));
+                const float2 tjl = make_float2(tl(r0 + kt + d + l), tl(rb + kt + d + l));
+                const float2 ncj = add2(v2_sub(mjh[d], tj), v2_sub(mjl[d], tjl));  // -(tj - mu_j)
+                const float2 p = z_mul(ci, ncj);                   // -ci cj
+                const float2 t = add2(ch[d], p);                   // Fast2Sum(ch, p)
+                const float2 z = v2_sub(t, ch[d]);
+                cl[d] = add2(cl[d], v2_sub(p, z));
+                ch[d] = t;
+            }
+        }
+    }
+
+    float ca[Z_D], cb[Z_D];
+#pragma unroll
+    for (int d = 0; d < Z_D; ++d) { ca[d] = NONE; cb[d] = NONE; }
+
+    // score of the current state: q = 1 - cov inv_i inv_j (cov = -(ch + cl))
+    auto score = [&](float2 iI, float2 jI, int d) {
+        const float2 w = z_mul(iI, jI);
+        return fma2(cl[d], w, fma2(ch[d], w, ONE));
+    };
+
+    // Chunk c covers stream-local rows u0c + 1 .. u0c + RC (row 0, the anchor, is
+    // done in chunk 0); blocks of 8 rows keep every window 16-byte aligned.
+    const int nchunks_cta = Hs > 1 ? (Hs - 1 + Z_RC - 1) / Z_RC : 1;
+    int ulast = 0;
+    for (int c = 0; c < nchunks_cta; ++c) {
+        const int u0c = c * Z_RC;
+        __syncthreads();  // the previous chunk is done with shared memory
+        {
+            // j side: element x = partner index (j - 1) - y, y = r_s + u0c + k0 - 1
+            const long long ya = r0 + u0c + k0 - 1, yb = ya + Hs;
+            auto gv = [&](const float *p, long long g) -> float { return (g >= 0 && g < a.N) ? p[g] : 0.f; };
+            for (int x = tid; x < Z_KW + Z_RC + 16; x += Z_NT) {
+                const int px = v2_jpos(x);
+                JF[px] = make_float2(gv(a.df, ya + x), gv(a.df, yb + x));
+                JG[px] = make_float2(gv(a.dg, ya + x), gv(a.dg, yb + x));
+                JI[px] = make_float2(gv(a.inv, ya + x + 1), gv(a.inv, yb + x + 1));
+            }
+            // i side: chunk row ul uses df, dg of window i - 1 and inv of window i
+            const long long ia = r0 + u0c, ib = rb + u0c;
+            for (int ul = tid; ul < Z_RC + 16; ul += Z_NT) {
+                IF[ul] = make_float2(gv(a.df, ia + ul - 1), gv(a.df, ib + ul - 1));
+                IG[ul] = make_float2(gv(a.dg, ia + ul - 1), gv(a.dg, ib + ul - 1));
+                II[ul] = make_float2(gv(a.inv, ia + ul), gv(a.inv, ib + ul));
+            }
+            // A target without a candidate yet gets the largest finite threshold, not
+            // +inf: a slot that saw only flat windows (NaN scores) holds +inf and
+            // must not pass the unguarded tests of the fast blocks.
+            auto thr_of = [&](long long g) -> float {
+                if (g < 0 || g >= a.N) return 0.f;
+                const unsigned long long key = a.keys[g];
+                return key == KEY_NONE ? THR_OPEN : v2_thr_form(static_cast<unsigned>(key >> 32));
+            };
+            for (int ul = tid; ul < Z_RC + 8; ul += Z_NT) {
+                thr_r[ul] = thr_of(ia + ul);
+                thr_r[Z_RC + 8 + ul] = thr_of(ib + ul);
+            }
+            for (int x = tid; x < Z_KW + Z_RC + 16; x += Z_NT) {
+                thr_ca[v2_cpos(x)] = thr_of(ia + k0 + x);
+                thr_cb[v2_cpos(x)] = thr_of(ib + k0 + x);
+            }
+        }
+        __syncthreads();
+        if (!active || u0c >= steps) continue;
+
+        float *trb_base = thr_r + (Z_RC + 8);
+        auto col_tgt = [&](int uc, int sb) { return (sb ? rb : r0) + kt + uc; };
+        auto row_tgt = [&](int u, int sb) { return (sb ? rb : r0) + u; };
+        // masked processing of stream-local row u = u0c + ul (state already stepped)
+        auto masked_row = [&](int u, int ul, int j) {
+            float ta = NONE, tb = NONE;
+#pragma unroll
+            for (int d = 0; d < Z_D; ++d) {
+                const float2 q = score(II[ul], JI[v2_jpos(jb + d + ul)], d);
+                const float va = (d < nd && u + d < lim) ? v2_tag(q.x, d) : NONE;
+                const float vb = (d < nd && u + d < lim_b) ? v2_tag(q.y, d) : NONE;
+                ta = fminf(ta, va);
+                tb = fminf(tb, vb);
+                const int sl = (j + d) % Z_D;
+                ca[sl] = d == Z_D - 1 ? va : fminf(ca[sl], va);
+                cb[sl] = d == Z_D - 1 ? vb : fminf(cb[sl], vb);
+            }
+            // NONE (no valid cell) and NaN (a flat window) are never offered
+            if (ta != NONE && ta <= thr_r[ul]) v2_emit(a.keys, thr_r, ul, row_tgt(u, 0), ta, kt, 1);
+            if (tb != NONE && tb <= trb_base[ul]) v2_emit(a.keys, trb_base, ul, row_tgt(u, 1), tb, kt, 1);
+            const int ci = v2_cpos(jb + ul);
+            if (ca[j] != NONE && ca[j] <= thr_ca[ci]) v2_emit(a.keys, thr_ca, ci, col_tgt(u, 0), ca[j], kt, 0);
+            if (cb[j] != NONE && cb[j] <= thr_cb[ci]) v2_emit(a.keys, thr_cb, ci, col_tgt(u, 1), cb[j], kt, 0);
+            ca[j] = NONE;
+            cb[j] = NONE;
+        };
+        // one covariance step into chunk row ul, partner window offset o
+        auto step = [&](int ul, const float2 *WF, const float2 *WG, int o) {
+            const float2 fi = IF[ul], gi = IG[ul];
+#pragma unroll
+            for (int d = 0; d < Z_D; ++d) {
+                const float2 inc = fma2(fi, WG[o + d], z_mul(WF[o + d], gi));  // df_i dg_j + df_j dg_i
+                const float2 t = v2_sub(ch[d], inc);                               // Fast2Sum(ch, -inc)
+                const float2 z = v2_sub(t, ch[d]);
+                cl[d] = v2_sub(cl[d], add2(inc, z));
+                ch[d] = t;
+            }
+        };
+
+        if (c == 0) masked_row(0, 0, 0);  // the anchor row
+        const float4 *JF4 = reinterpret_cast<const float4 *>(JF);
+        const float4 *JG4 = reinterpret_cast<const float4 *>(JG);
+        const float4 *JI4 = reinterpret_cast<const float4 *>(JI);
+        for (int ulb = 0; ulb < Z_RC; ulb += Z_D) {
+            const int ufirst = u0c + ulb + 1;
+            if (ufirst >= steps) break;
+            if (u0c + ulb + Z_D < ufast) {
+                // ---- fast block: rows ufirst .. ufirst + 7, all cells valid
+                float2 WF[2 * Z_D], WG[2 * Z_D], WI[2 * Z_D];
+                const int qb = 5 * ((jb + ulb) >> 3);
+#pragma unroll
+                for (int q = 0; q < Z_D; ++q) {
+                    const int o = qb + q + (q >= 4 ? 1 : 0);
+                    const float4 f4 = JF4[o], g4 = JG4[o], i4 = JI4[o];
+                    WF[2 * q] = make_float2(f4.x, f4.y);
+                    WF[2 * q + 1] = make_float2(f4.z, f4.w);
+                    WG[2 * q] = make_float2(g4.x, g4.y);
+                    WG[2 * q + 1] = make_float2(g4.z, g4.w);
+                    WI[2 * q] = make_float2(i4.x, i4.y);
+                    WI[2 * q + 1] = make_float2(i4.z, i4.w);
+                }
+                const float *tra = thr_r + ulb, *trb = trb_base + ulb;
+                const float *tca = thr_ca + v2_cpos(jb + ulb), *tcb = thr_cb + v2_cpos(jb + ulb);
+#pragma unroll
+                for (int pr = 0; pr < Z_D / 2; ++pr) {
+                    const int ul0 = 2 * pr + 1, ul1 = ul0 + 1;  // block-local rows
+                    const int cp0 = ul0 + (ul0 >> 3), cp1 = ul1 + (ul1 >> 3);
+                    float t0a[Z_D], t0b[Z_D], t1a[Z_D], t1b[Z_D];
+                    float2 q[Z_D];
+                    step(ulb + ul0, WF, WG, ul0);
+#pragma unroll
+                    for (int d = 0; d < Z_D; ++d) q[d] = score(II[ulb + ul0], WI[ul0 + d], d);
+                    v2_tag8(t0a, q, false, tag_mask);
+                    v2_tag8(t0b, q, true, tag_mask);
+                    step(ulb + ul1, WF, WG, ul1);
+#pragma unroll
+                    for (int d = 0; d < Z_D; ++d) q[d] = score(II[ulb + ul1], WI[ul1 + d], d);
+                    v2_tag8(t1a, q, false, tag_mask);
+                    v2_tag8(t1b, q, true, tag_mask);
+                    const float r0a = v2_min8(t0a), r0b = v2_min8(t0b), r1a = v2_min8(t1a), r1b = v2_min8(t1b);
+                    const int j0 = ul0 % Z_D, j1 = ul1 % Z_D;
+#pragma unroll
+                    for (int jj = 0; jj < Z_D; ++jj) {
+                        const int sl = (j0 + jj) % Z_D;
+                        if (jj == 0) {
+                            ca[sl] = fminf(ca[sl], t0a[0]);
+                            cb[sl] = fminf(cb[sl], t0b[0]);
+                        } else if (jj < Z_D - 1) {
+                            ca[sl] = min3f(ca[sl], t0a[jj], t1a[jj - 1]);
+                            cb[sl] = min3f(cb[sl], t0b[jj], t1b[jj - 1]);
+                        } else {
+                            ca[sl] = fminf(t0a[jj], t1a[jj - 1]);
+                            cb[sl] = fminf(t0b[jj], t1b[jj - 1]);
+                        }
+                    }
+                    const int any = v2_any_le(r0a, tra[ul0], r0b, trb[ul0], r1a, tra[ul1], r1b, trb[ul1], ca[j0],
+                                              tca[cp0], cb[j0], tcb[cp0], ca[j1], tca[cp1], cb[j1], tcb[cp1]);
+                    if (__builtin_expect(any != 0, 0)) {
+                        const int u0 = u0c + ulb + ul0, u1 = u0 + 1;
+                        const int r_0 = ulb + ul0, r_1 = r_0 + 1;  // chunk-local rows
+                        if (r0a <= tra[ul0]) v2_emit(a.keys, thr_r, r_0, row_tgt(u0, 0), r0a, kt, 1);
+                        if (r0b <= trb[ul0]) v2_emit(a.keys, trb_base, r_0, row_tgt(u0, 1), r0b, kt, 1);
+                        if (r1a <= tra[ul1]) v2_emit(a.keys, thr_r, r_1, row_tgt(u1, 0), r1a, kt, 1);
+                        if (r1b <= trb[ul1]) v2_emit(a.keys, trb_base, r_1, row_tgt(u1, 1), r1b, kt, 1);
+                        const int ci0 = v2_cpos(jb + r_0), ci1 = v2_cpos(jb + r_1);
+                        if (ca[j0] <= tca[cp0]) v2_emit(a.keys, thr_ca, ci0, col_tgt(u0, 0), ca[j0], kt, 0);
+                        if (cb[j0] <= tcb[cp0]) v2_emit(a.keys, thr_cb, ci0, col_tgt(u0, 1), cb[j0], kt, 0);
+                        if (ca[j1] <= tca[cp1]) v2_emit(a.keys, thr_ca, ci1, col_tgt(u1, 0), ca[j1], kt, 0);
+                        if (cb[j1] <= tcb[cp1]) v2_emit(a.keys, thr_cb, ci1, col_tgt(u1, 1), cb[j1], kt, 0);
+                    }
+                    ca[j0] = t1a[Z_D - 1];
+                    cb[j0] = t1b[Z_D - 1];
+                    ca[j1] = NONE;
+                    cb[j1] = NONE;
+                }
+                ulast = u0c + ulb + Z_D;
+            } else {
+                // ---- masked rows, one at a time (u % 8 stays a compile-time constant)
+#pragma unroll
+                for (int ui = 1; ui <= Z_D; ++ui) {
+                    const int u = u0c + ulb + ui;
+                    if (u >= steps) break;
+                    const int ul = ulb + ui;
+                    float2 WFr[Z_D], WGr[Z_D];
+#pragma unroll
+                    for (int d = 0; d < Z_D; ++d) {
+                        const int px = v2_jpos(jb + d + ul);
+                        WFr[d] = JF[px];
+                        WGr[d] = JG[px];
+                    }
+                    step(ul, WFr, WGr, 0);
+                    masked_row(u, ul, ui % Z_D);
+                    ulast = u;
+                }
+            }
+        }
+        if (ulast == steps - 1 && ulast >= u0c && (ulast > u0c || c == 0)) {
+            // this thread's last row is in this chunk: flush the open columns
+            // (slot sl holds column ulast + ((sl - ulast) mod D))
+#pragma unroll
+            for (int sl = 0; sl < Z_D; ++sl) {
+                const int delta = ((sl - ulast) % Z_D + Z_D) % Z_D;
+                if (delta == 0) continue;
+                const int uc = ulast + delta;
+                const int ci = v2_cpos(jb + uc - u0c);
+                if (ca[sl] != NONE && ca[sl] <= thr_ca[ci]) v2_emit(a.keys, thr_ca, ci, col_tgt(uc, 0), ca[sl], kt, 0);
+                if (cb[sl] != NONE && cb[sl] <= thr_cb[ci]) v2_emit(a.keys, thr_cb, ci, col_tgt(uc, 1), cb[sl], kt, 0);
+            }
+        }
+    }
+}
+
+}  // namespace mpk
