@@ -123,15 +123,23 @@ def oracle_sample(series: W.Series, target_s: float = 12.0):
     oracle.build()
     T = series.T.astype(np.float64)
     k0 = series.excl + 1
+
+    def sweep(k_range):
+        if series.dist == W.EUCLID:
+            return oracle.aamp(T, series.m, series.excl, k_range=k_range)
+        if series.dist == W.PNORM:
+            return oracle.pnorm(T, series.m, series.excl, series.p, k_range=k_range)
+        return oracle.acamp_centred(T, series.m, series.excl, k_range=k_range)
+
     # calibrate on a short range
-    kc = 256
+    kc = min(256, max(1, series.N - k0))
     t0 = time.perf_counter()
-    oracle.aamp(T, series.m, series.excl, k_range=(k0, k0 + kc))
+    sweep((k0, k0 + kc))
     dt = time.perf_counter() - t0
     rate = kc * series.N / max(dt, 1e-6)  # cells/s, roughly
     K = int(min(series.N - k0, max(kc, target_s * rate / series.N)))
     t0 = time.perf_counter()
-    oracle.aamp(T, series.m, series.excl, k_range=(k0, k0 + K))
+    sweep((k0, k0 + K))
     dt = time.perf_counter() - t0
     cells = sum(series.N - k for k in range(k0, k0 + K))
     return {"value": cells / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
@@ -143,7 +151,14 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    series = W.aamp_1m(seed=1)
+    if args.workload == "batch_4096":
+        b = W.batch_4096()
+        series = max(b.series, key=lambda x: x.n)  # the oracle's sample: the longest series
+        config = batch_config(b)
+    else:
+        make, desc, _ = WORKLOADS[args.workload]
+        series = make(1, args.n)
+        config = workload_config(series, desc)
     runs = []
     for _ in range(max(0, args.warmup_ref)):
         oracle_sample(series, target_s=2.0)
@@ -155,7 +170,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, len(runs)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(series),
+            "data": "synthetic", "config": config,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": runs[0]["cores"], "kind": "oracle",
                              "sample": runs[0]["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -186,6 +201,103 @@ def workload_config(series: W.Series, desc: str = WORKLOADS["aamp_1m"][1], preci
             "l2": "flushed before every timed step (512 MiB write)"}
 
 
+def batch_config(b: W.Batch) -> dict:
+    ns = np.array([x.n for x in b.series])
+    return {"workload": f"{b.name} (4,096 float32 random walks, m in {{32, 64, 128}}, "
+                        f"half Euclidean / half z-normalised, one graph launch)",
+            "series": len(b.series), "samples": int(ns.sum()), "cells_per_step": int(b.cells),
+            "precision": "fp32 sweep (re-anchored / compensated), fp64 polish",
+            "l2": "inputs (553 MB) and outputs larger than L2; L2 flushed before every timed step"}
+
+
+def bench_batch(args, torch, mp, lib, dev, stream, rank, ws):
+    """The 4,096-series batch: one mp_batch_run (one graph launch) per step."""
+    b = W.batch_4096(seed=4 + rank)
+    plan = mp.BatchPlan([x.n for x in b.series], [x.m for x in b.series], [x.dist for x in b.series],
+                        [x.excl for x in b.series])
+    T_host = torch.from_numpy(np.concatenate([x.T for x in b.series]).astype(np.float32)).pin_memory()
+    T = T_host.to(dev)
+    P = torch.empty(plan.windows, dtype=torch.float64, device=dev)
+    I = torch.empty(plan.windows, dtype=torch.int64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        plan.run(T, out=(P, I))
+    torch.cuda.synchronize()
+    mp.sync_status()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = lib.mp_launch_count()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        ev[k][0].record(stream)
+        plan.run(T, out=(P, I))
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = lib.mp_launch_count() - launches0
+    clk = clocks.stop()
+    mp.sync_status()
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    total_ms = float(sum(step_ms))
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    cells = b.cells
+    value = ws * cells * args.steps / (total_ms * 1e-3) / 1e9
+
+    # end to end: host series in, host profiles out
+    P_host = torch.empty(plan.windows, dtype=torch.float64).pin_memory()
+    I_host = torch.empty(plan.windows, dtype=torch.int64).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        T.copy_(T_host, non_blocking=True)
+        plan.run(T, out=(P, I))
+        P_host.copy_(P, non_blocking=True)
+        I_host.copy_(I, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_value = ws * cells / (e2e_ms * 1e-3) / 1e9
+
+    pk, src = peaks()
+    f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_cells = sms * FP32_LANES_PER_SM * f_max / FP32_INSTR_PER_CELL / 1e9
+    achieved = cells / (total_ms / args.steps * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_cells, "unit": UNIT,
+            "frac": achieved / peak_cells, "traffic": None,
+            "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {f_max/1e6:.0f} MHz "
+                           f"({src} sm_max_mhz) / {FP32_INSTR_PER_CELL} FP32 instructions per cell",
+            "kernel": "whole batch graph (statistics, persistent sweeps, finalize): a lower bound "
+                      "for the sweep kernels", "kernel_ms": total_ms / args.steps,
+            "tiles": plan.tiles}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": batch_config(b), "roofline": roof, "clocks": clk, "gpu_launches": int(launches),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(T_host.numel() * 4),
+                    "d2h_bytes_per_step": int(plan.windows * 16), "ms_per_step": e2e_ms}}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        longest = max(b.series, key=lambda x: x.n)
+        cb = oracle_sample(longest, target_s=args.ref_seconds)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    plan.close()
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -196,7 +308,7 @@ def main():
     ap.add_argument("--warmup-ref", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=1 << 20)
-    ap.add_argument("--workload", default="aamp_1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="aamp_1m", choices=sorted(WORKLOADS) + ["batch_4096"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--k-range", type=int, nargs=2, default=None,
                     help="sweep only diagonals [k0, k1) (for timing the FP64 sweep on a slice)")
@@ -217,9 +329,16 @@ def main():
     dev = torch.device("cuda", local)
     lib = mp.load()
 
+    if args.workload == "batch_4096":
+        line = bench_batch(args, torch, mp, lib, dev, torch.cuda.current_stream(dev), rank, ws)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if ws > 1:
+            dist.destroy_process_group()
+        return
     make, desc, instr_per_cell = WORKLOADS[args.workload]
     series = make(1 + rank, args.n)
-    dist = {W.EUCLID: "euclid", W.PNORM: "pnorm", W.ZNORM: "znorm"}[series.dist]
+    dname = {W.EUCLID: "euclid", W.PNORM: "pnorm", W.ZNORM: "znorm"}[series.dist]
     T_host = torch.from_numpy(series.T).pin_memory()
     T = T_host.to(dev)
     N = series.N
@@ -233,7 +352,7 @@ def main():
         kw["k_range"] = tuple(args.k_range)
 
     def step():
-        mp.profile(T, series.m, series.excl, dist, series.p, out=(P, I), **kw)
+        mp.profile(T, series.m, series.excl, dname, series.p, out=(P, I), **kw)
 
     for _ in range(args.warmup):
         step()
@@ -290,7 +409,7 @@ def main():
     e0.record(stream)
     for _ in range(e2e_steps):
         T_dev2.copy_(T_host, non_blocking=True)
-        mp.profile(T_dev2, series.m, series.excl, dist, series.p, out=(P, I), **kw)
+        mp.profile(T_dev2, series.m, series.excl, dname, series.p, out=(P, I), **kw)
         P_host.copy_(P, non_blocking=True)
         I_host.copy_(I, non_blocking=True)
     e1.record(stream)
@@ -304,12 +423,12 @@ def main():
         k0 = series.excl + 1
         k1 = min(series.N, k0 + args.fp64_diagonals)
         kw64 = {"precision": "fp64", "k_range": (k0, k1)}
-        mp.profile(T, series.m, series.excl, dist, series.p, out=(P, I), **kw64)  # warm-up
+        mp.profile(T, series.m, series.excl, dname, series.p, out=(P, I), **kw64)  # warm-up
         ms64 = []
         for k in range(2):
             flush.fill_(k & 0xff)
             lib.mp_set_sweep_events(ctypes_event(sw[k][0]), ctypes_event(sw[k][1]))
-            mp.profile(T, series.m, series.excl, dist, series.p, out=(P, I), **kw64)
+            mp.profile(T, series.m, series.excl, dname, series.p, out=(P, I), **kw64)
             lib.mp_set_sweep_events(None, None)
             torch.cuda.synchronize()
             ms64.append(sw[k][0].elapsed_time(sw[k][1]))

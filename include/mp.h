@@ -175,6 +175,70 @@ mp_status mp_set_sweep_events(void *ev_start, void *ev_end);
 mp_status mp_aamp_noalloc(const void *T, int dtype, int64_t n, int32_t m, int64_t excl,
                           double *P, int64_t *I, const mp_options *opt, void *stream);
 
+/* ---- Batches: many independent profiles in one graph launch ---------------
+ *
+ * The paper treats one series at a time (Algorithms 1-3); a batch runs the
+ * same computation for S independent series, each with its own m, exclusion
+ * zone and distance, as one CUDA graph: FP64 window statistics for the
+ * z-normalised series, then persistent sweep kernels that take the tiles of
+ * every series from one queue per kernel (longest tiles first, one atomic
+ * ticket per tile), then the finalize/polish of every window.
+ *
+ * Layout.  T is the S series concatenated (FP32): series s is
+ * T[t_offsets[s] .. t_offsets[s+1]).  P and I are the S profiles
+ * concatenated: series s has N_s = n_s - m_s + 1 entries starting at
+ * w_s = N_0 + ... + N_{s-1}, and I holds indices within the series (or -1).
+ * mp_batch_windows() gives the total length sum_s N_s.
+ */
+typedef struct mp_batch_desc {
+    uint32_t struct_size;      /* = sizeof(mp_batch_desc)                              */
+    int32_t num_series;        /* S >= 1                                               */
+    const int64_t *t_offsets;  /* host, S + 1 non-decreasing sample offsets, n_s >= 1  */
+    const int32_t *m;          /* host, S window lengths, 1 <= m_s <= n_s              */
+    const uint8_t *dist;       /* host, S mp_dist values                               */
+    const int64_t *excl;       /* host, S exclusion zones >= 0                         */
+    double p;                  /* exponent of every MP_DIST_PNORM series (>= 1)        */
+    int32_t dtype;             /* MP_F32 (the only batch input type)                   */
+    int32_t reserved0;
+} mp_batch_desc;
+
+typedef struct mp_batch_plan mp_batch_plan;
+
+/* Validate desc, split every series into sweep tiles, sort the tile queues
+ * and upload them (with the per-series table) to device memory that the plan
+ * owns; *ws_bytes receives the workspace size mp_batch_run needs.  The plan
+ * belongs to the current device.  opt may be NULL; the batch runs the FP32
+ * sweep with the default re-anchor interval and whole diagonal ranges, so
+ * opt->precision must be MP_PREC_FP32, reanchor 0, k_begin = k_end = 0 (else
+ * MP_ERR_UNSUPPORTED); opt->polish is honoured.  desc is not kept.
+ * Errors: MP_ERR_INVALID_ARG (desc, sizes, dist, p), MP_ERR_UNSUPPORTED
+ * (dtype, options, N_s >= 2^31, more than 2^32 - 1 tiles in a queue, m_s too
+ * large for shared memory), MP_ERR_CUDA (allocation or copy failed; nothing
+ * is leaked).  Validation happens before any CUDA call. */
+mp_status mp_batch_plan_create(const mp_batch_desc *desc, const mp_options *opt,
+                               mp_batch_plan **plan, size_t *ws_bytes);
+
+/* Enqueue the whole batch on `stream` as one graph launch.
+ *   T   device, t_offsets[S] floats (4-byte aligned)
+ *   P   device, mp_batch_windows(plan) doubles;  I  device, as many int64
+ *   ws  device workspace, 256-byte aligned, ws_bytes >= the plan's size
+ * The graph is built on the first run and rebuilt whenever T, P, I or ws
+ * differ from the previous run's.  A plan is not thread-safe.  The queue
+ * tickets live in ws, so two runs in flight at the same time (on different
+ * streams) need different workspaces. */
+mp_status mp_batch_run(mp_batch_plan *plan, const void *T, double *P, int64_t *I,
+                       void *ws, size_t ws_bytes, void *stream);
+
+/* sum_s N_s (the length of P and I), or -1 for a NULL plan. */
+int64_t mp_batch_windows(const mp_batch_plan *plan);
+
+/* Tiles in the plan's queues (all kernels), or -1 for a NULL plan. */
+int64_t mp_batch_tiles(const mp_batch_plan *plan);
+
+/* Free the plan's device memory and graph.  NULL is a no-op.  Call it after
+ * the plan's last run has completed. */
+mp_status mp_batch_plan_destroy(mp_batch_plan *plan);
+
 #ifdef __cplusplus
 }
 #endif

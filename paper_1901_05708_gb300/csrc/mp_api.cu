@@ -12,6 +12,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "mp.h"
 #include "mp_device.cuh"
@@ -20,6 +22,7 @@
 #include "mp_sweep2.cuh"
 #include "mp_sweep_z2.cuh"
 #include "mp_launch.cuh"
+#include "mp_batch.cuh"
 
 namespace {
 
@@ -559,6 +562,405 @@ uint64_t mp_launch_count(void) { return g_launches.load(); }
 mp_status mp_set_sweep_events(void *ev_start, void *ev_end) {
     g_ev_start = static_cast<cudaEvent_t>(ev_start);
     g_ev_end = static_cast<cudaEvent_t>(ev_end);
+    return MP_OK;
+}
+
+}  // extern "C"
+
+// ---- a7: batches -----------------------------------------------------------------------
+struct mp_batch_plan {
+    enum { Q_FAST2 = 0, Q_Z = 1, Q_GEN2 = 2, Q_GENP = 3, NQ = 4 };
+    int device = -1;
+    int S = 0;
+    double p = 2.0;
+    int polish = 1;
+    int genp_kind = mpk::K_P2;  // exponent kind of the p-norm generic queue
+    long long windows = 0, zwindows = 0, samples = 0;
+    std::vector<mpk::BatchSeries> series;
+    std::vector<long long> w_start;
+    std::vector<mpk::BatchTile> tiles[NQ];
+    size_t smem[NQ] = {};
+    int grid[NQ] = {};
+    // device copies (owned)
+    mpk::BatchSeries *d_series = nullptr;
+    long long *d_wstart = nullptr;
+    mpk::BatchTile *d_tiles[NQ] = {};
+    // workspace layout
+    size_t o_keys = 0, o_tickets = 0, o_mu = 0, o_S = 0, o_flat = 0, o_df = 0, o_dg = 0, o_inv = 0, o_muh = 0,
+           o_mul = 0, ws_bytes = 0;
+    // graph cache
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void *g_T = nullptr;
+    const void *g_P = nullptr;
+    const void *g_I = nullptr;
+    const void *g_ws = nullptr;
+    int nodes = 0;
+};
+
+namespace {
+
+void batch_free(mp_batch_plan *pl) {
+    if (!pl) return;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->cap) cudaStreamDestroy(pl->cap);
+    if (pl->d_series) cudaFree(pl->d_series);
+    if (pl->d_wstart) cudaFree(pl->d_wstart);
+    for (auto *t : pl->d_tiles)
+        if (t) cudaFree(t);
+    delete pl;
+}
+
+// Tiles of one series for a sweep whose bands hold KW diagonals and whose
+// tiles hold R rows (band b: L - b KW rows), with cost = rows x diagonals.
+void batch_tiles(std::vector<std::pair<long long, mpk::BatchTile>> &out, int s, long long L, int KW, int R) {
+    if (L <= 0) return;
+    const long long nb = (L + KW - 1) / KW;
+    for (long long b = 0; b < nb; ++b) {
+        const long long Lb = L - b * KW;
+        const long long nd = std::min<long long>(KW, Lb);
+        const long long nt = (Lb + R - 1) / R;
+        for (long long rt = 0; rt < nt; ++rt) {
+            const long long rows = std::min<long long>(R, Lb - rt * R);
+            out.push_back({rows * nd, mpk::BatchTile{s, static_cast<int>(b), static_cast<int>(rt), 0}});
+        }
+    }
+}
+
+mp_status batch_validate(const mp_batch_desc *d, const mp_options *opt, mp_options &o) {
+    if (!d) return fail(MP_ERR_INVALID_ARG, "desc is NULL");
+    if (d->struct_size != sizeof(mp_batch_desc))
+        return fail(MP_ERR_INVALID_ARG, "mp_batch_desc.struct_size %u != %zu", d->struct_size, sizeof(mp_batch_desc));
+    if (d->num_series < 1) return fail(MP_ERR_INVALID_ARG, "num_series = %d < 1", d->num_series);
+    if (!d->t_offsets || !d->m || !d->dist || !d->excl) return fail(MP_ERR_INVALID_ARG, "NULL array in desc");
+    if (d->dtype != MP_F32) {
+        if (d->dtype == MP_F64) return fail(MP_ERR_UNSUPPORTED, "batches take float32 series only");
+        return fail(MP_ERR_INVALID_ARG, "dtype %d", d->dtype);
+    }
+    if (opt) {
+        if (opt->struct_size != sizeof(mp_options))
+            return fail(MP_ERR_INVALID_ARG, "mp_options.struct_size %u != %zu", opt->struct_size, sizeof(mp_options));
+        o = *opt;
+    } else {
+        mp_options_default(&o);
+    }
+    if (o.precision != MP_PREC_FP32) return fail(MP_ERR_UNSUPPORTED, "batches run the FP32 sweep only");
+    if (o.reanchor != 0) return fail(MP_ERR_UNSUPPORTED, "batches use the default re-anchor interval");
+    if (o.k_begin != 0 || o.k_end != 0) return fail(MP_ERR_UNSUPPORTED, "batches sweep whole diagonal ranges");
+    if (o.polish != 0 && o.polish != 1) return fail(MP_ERR_INVALID_ARG, "polish %d", o.polish);
+    if (d->t_offsets[0] < 0) return fail(MP_ERR_INVALID_ARG, "t_offsets[0] < 0");
+    bool any_p = false;
+    for (int s = 0; s < d->num_series; ++s) {
+        const long long n = d->t_offsets[s + 1] - d->t_offsets[s];
+        const int m = d->m[s];
+        if (n < 1) return fail(MP_ERR_INVALID_ARG, "series %d: n = %lld < 1", s, n);
+        if (m < 1 || m > n) return fail(MP_ERR_INVALID_ARG, "series %d: m = %d outside [1, %lld]", s, m, n);
+        if (d->dist[s] > MP_DIST_ZNORM) return fail(MP_ERR_INVALID_ARG, "series %d: dist %d", s, d->dist[s]);
+        if (d->dist[s] == MP_DIST_ZNORM && m < 2)
+            return fail(MP_ERR_INVALID_ARG, "series %d: z-normalised distance needs m >= 2", s);
+        if (d->excl[s] < 0) return fail(MP_ERR_INVALID_ARG, "series %d: excl < 0", s);
+        if (n - m + 1 >= (1ll << 31) - 1) return fail(MP_ERR_UNSUPPORTED, "series %d: N >= 2^31 - 1", s);
+        any_p |= d->dist[s] == MP_DIST_PNORM;
+    }
+    if (any_p && !(d->p >= 1.0 && std::isfinite(d->p)))
+        return fail(MP_ERR_INVALID_ARG, "p = %g, need a finite p >= 1", d->p);
+    return MP_OK;
+}
+
+template <typename K>
+void batch_grid(mp_batch_plan *pl, int q, K kernel, int nt, int sms) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nt, pl->smem[q]) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const long long want = static_cast<long long>(per_sm) * sms;
+    pl->grid[q] = static_cast<int>(std::min<long long>(want, static_cast<long long>(pl->tiles[q].size())));
+}
+
+template <int KIND>
+cudaError_t launch_gen_batch(const mp_batch_plan *pl, const mpk::BatchData &bd, const mpk::BatchQueue &q, int qi,
+                             cudaStream_t st) {
+    mpk::sweep_batch_kernel<KIND><<<pl->grid[qi], mpk::SW_NT, pl->smem[qi], st>>>(bd, q, mpk::device_error_ptr());
+    return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t gen_batch_attr(mp_batch_plan *pl, int qi, int sms) {
+    cudaError_t e = cudaFuncSetAttribute(mpk::sweep_batch_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(pl->smem[qi]));
+    if (e == cudaSuccess) batch_grid(pl, qi, mpk::sweep_batch_kernel<KIND>, mpk::SW_NT, sms);
+    return e;
+}
+
+cudaError_t gen_dispatch_attr(mp_batch_plan *pl, int qi, int kind, int sms) {
+    switch (kind) {
+        case mpk::K_P1: return gen_batch_attr<mpk::K_P1>(pl, qi, sms);
+        case mpk::K_P3: return gen_batch_attr<mpk::K_P3>(pl, qi, sms);
+        case mpk::K_PG: return gen_batch_attr<mpk::K_PG>(pl, qi, sms);
+        default: return gen_batch_attr<mpk::K_P2>(pl, qi, sms);
+    }
+}
+
+cudaError_t gen_dispatch_launch(const mp_batch_plan *pl, const mpk::BatchData &bd, const mpk::BatchQueue &q,
+                                int qi, int kind, cudaStream_t st) {
+    switch (kind) {
+        case mpk::K_P1: return launch_gen_batch<mpk::K_P1>(pl, bd, q, qi, st);
+        case mpk::K_P3: return launch_gen_batch<mpk::K_P3>(pl, bd, q, qi, st);
+        case mpk::K_PG: return launch_gen_batch<mpk::K_PG>(pl, bd, q, qi, st);
+        default: return launch_gen_batch<mpk::K_P2>(pl, bd, q, qi, st);
+    }
+}
+
+// Record the batch on the plan's capture stream and instantiate it.
+mp_status batch_build_graph(mp_batch_plan *pl, const void *T, double *P, int64_t *I, void *ws) {
+    char *w = static_cast<char *>(ws);
+    mpk::BatchData bd{};
+    bd.series = pl->d_series;
+    bd.w_start = pl->d_wstart;
+    bd.S = pl->S;
+    bd.windows = pl->windows;
+    bd.T = static_cast<const float *>(T);
+    bd.keys = reinterpret_cast<unsigned long long *>(w + pl->o_keys);
+    if (pl->zwindows > 0) {
+        bd.mu = reinterpret_cast<double *>(w + pl->o_mu);
+        bd.Sx = reinterpret_cast<double *>(w + pl->o_S);
+        bd.flat = reinterpret_cast<unsigned char *>(w + pl->o_flat);
+        bd.df = reinterpret_cast<float *>(w + pl->o_df);
+        bd.dg = reinterpret_cast<float *>(w + pl->o_dg);
+        bd.inv = reinterpret_cast<float *>(w + pl->o_inv);
+        bd.muh = reinterpret_cast<float *>(w + pl->o_muh);
+        bd.mul = reinterpret_cast<float *>(w + pl->o_mul);
+    }
+    bd.P = P;
+    bd.I = reinterpret_cast<long long *>(I);
+    bd.p = pl->p;
+    bd.polish = pl->polish;
+    unsigned *tickets = reinterpret_cast<unsigned *>(w + pl->o_tickets);
+
+    cudaStream_t st = pl->cap;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    int nodes = 0;
+    const int gw = grid_for(pl->windows, mpk::PREP_NT);
+    mpk::batch_init_kernel<<<gw, mpk::PREP_NT, 0, st>>>(bd.keys, pl->windows, tickets, mp_batch_plan::NQ);
+    ++nodes;
+    if (pl->zwindows > 0) {
+        mpk::batch_zstats_kernel<<<gw, mpk::PREP_NT, 0, st>>>(bd);
+        mpk::batch_zoperands_kernel<<<gw, mpk::PREP_NT, 0, st>>>(bd);
+        nodes += 2;
+    }
+    for (int qi = 0; qi < mp_batch_plan::NQ; ++qi) {
+        if (pl->tiles[qi].empty()) continue;
+        const mpk::BatchQueue q{pl->d_tiles[qi], static_cast<unsigned>(pl->tiles[qi].size()), tickets + qi};
+        if (qi == mp_batch_plan::Q_FAST2)
+            mpk::sweep2_batch_kernel<<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
+        else if (qi == mp_batch_plan::Q_Z)
+            mpk::sweepz_batch_kernel<<<pl->grid[qi], mpk::Z_NT, pl->smem[qi], st>>>(bd, q);
+        else
+            gen_dispatch_launch(pl, bd, q, qi, qi == mp_batch_plan::Q_GEN2 ? mpk::K_P2 : pl->genp_kind, st);
+        ++nodes;
+    }
+    mpk::batch_finalize_kernel<<<gw, mpk::PREP_NT, 0, st>>>(bd);
+    ++nodes;
+    const cudaError_t le = cudaGetLastError();
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(st, &graph);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(le != cudaSuccess ? le : e, "recording the batch graph");
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    pl->exec = exec;
+    pl->nodes = nodes;
+    pl->g_T = T;
+    pl->g_P = P;
+    pl->g_I = I;
+    pl->g_ws = ws;
+    return MP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mp_status mp_batch_plan_create(const mp_batch_desc *desc, const mp_options *opt, mp_batch_plan **plan,
+                               size_t *ws_bytes) {
+    g_err[0] = 0;
+    if (!plan) return fail(MP_ERR_INVALID_ARG, "plan is NULL");
+    *plan = nullptr;
+    mp_options o{};
+    mp_status s = batch_validate(desc, opt, o);
+    if (s != MP_OK) return s;
+
+    auto *pl = new mp_batch_plan();
+    pl->S = desc->num_series;
+    pl->p = desc->p;
+    pl->polish = o.polish;
+    if (desc->p == 1.0) pl->genp_kind = mpk::K_P1;
+    else if (desc->p == 2.0) pl->genp_kind = mpk::K_P2;
+    else if (desc->p == 3.0) pl->genp_kind = mpk::K_P3;
+    else pl->genp_kind = mpk::K_PG;
+    std::vector<std::pair<long long, mpk::BatchTile>> q[mp_batch_plan::NQ];
+    int qmax_m[mp_batch_plan::NQ] = {}, qmax_Q[mp_batch_plan::NQ] = {};
+    pl->series.resize(pl->S);
+    pl->w_start.resize(pl->S + 1);
+    for (int si = 0; si < pl->S; ++si) {
+        mpk::BatchSeries &b = pl->series[si];
+        b.t_off = desc->t_offsets[si];
+        b.n = desc->t_offsets[si + 1] - desc->t_offsets[si];
+        b.m = desc->m[si];
+        b.N = b.n - b.m + 1;
+        b.k_first = desc->excl[si] + 1;
+        b.w_off = pl->windows;
+        pl->w_start[si] = pl->windows;
+        pl->windows += b.N;
+        const int dist = desc->dist[si];
+        const bool p2 = dist == MP_DIST_EUCLID || (dist == MP_DIST_PNORM && desc->p == 2.0);
+        b.dist = dist == MP_DIST_ZNORM ? mpk::FIN_ZNORM : dist == MP_DIST_PNORM ? mpk::FIN_PNORM : mpk::FIN_EUCLID;
+        b.z_off = -1;
+        choose_block(b.m, 0, mpk::SW_QMAX, b.B, b.Q);
+        b.RL = mpk::sweep_rows_leaving(mpk::BATCH_GEN_R, b.m);
+        const long long L = b.N - b.k_first;
+        int qi;
+        if (dist == MP_DIST_ZNORM) {
+            b.z_off = pl->zwindows;
+            pl->zwindows += b.N;
+            qi = mp_batch_plan::Q_Z;
+            batch_tiles(q[qi], si, L, mpk::Z_KW, mpk::Z_S);
+        } else if (p2 && b.m % 32 == 0 && mpk::sweep2_smem_bytes(b.m, mpk::V2_QMAX) <= 110 * 1024) {
+            qi = mp_batch_plan::Q_FAST2;
+            batch_tiles(q[qi], si, L, mpk::V2_KW, mpk::V2_R);
+        } else {
+            qi = p2 ? mp_batch_plan::Q_GEN2 : mp_batch_plan::Q_GENP;
+            batch_tiles(q[qi], si, L, mpk::SW_KW, mpk::BATCH_GEN_R);
+        }
+        if (L > 0) {
+            qmax_m[qi] = std::max(qmax_m[qi], b.m);
+            qmax_Q[qi] = std::max(qmax_Q[qi], b.Q);
+        }
+    }
+    pl->w_start[pl->S] = pl->windows;
+    pl->samples = desc->t_offsets[pl->S];
+    if (pl->genp_kind == mpk::K_P2) {  // p = 2: one generic queue
+        for (auto &t : q[mp_batch_plan::Q_GENP]) q[mp_batch_plan::Q_GEN2].push_back(t);
+        q[mp_batch_plan::Q_GENP].clear();
+        qmax_m[mp_batch_plan::Q_GEN2] = std::max(qmax_m[mp_batch_plan::Q_GEN2], qmax_m[mp_batch_plan::Q_GENP]);
+        qmax_Q[mp_batch_plan::Q_GEN2] = std::max(qmax_Q[mp_batch_plan::Q_GEN2], qmax_Q[mp_batch_plan::Q_GENP]);
+    }
+    for (int qi = 0; qi < mp_batch_plan::NQ; ++qi) {
+        if (q[qi].size() > 0xfffffffeull) {
+            batch_free(pl);
+            return fail(MP_ERR_UNSUPPORTED, "more than 2^32 - 2 tiles in one queue");
+        }
+        // longest tiles first; ties in series / band / row order
+        std::stable_sort(q[qi].begin(), q[qi].end(),
+                         [](const auto &a, const auto &b) { return a.first > b.first; });
+        pl->tiles[qi].reserve(q[qi].size());
+        for (auto &t : q[qi]) pl->tiles[qi].push_back(t.second);
+        if (qi == mp_batch_plan::Q_FAST2) pl->smem[qi] = mpk::sweep2_smem_bytes(std::max(qmax_m[qi], 32), mpk::V2_QMAX);
+        else if (qi == mp_batch_plan::Q_Z) pl->smem[qi] = mpk::sweepz_smem_bytes();
+        else pl->smem[qi] = mpk::sweep_smem_bytes(mpk::BATCH_GEN_R, std::max(qmax_m[qi], 1), std::max(qmax_Q[qi], 1), false);
+        if (!pl->tiles[qi].empty() && pl->smem[qi] > 227 * 1024) {
+            batch_free(pl);
+            return fail(MP_ERR_UNSUPPORTED, "m = %d needs %zu bytes of shared memory", qmax_m[qi], pl->smem[qi]);
+        }
+    }
+    // workspace
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t at = off; off += up(bytes); return at; };
+    pl->o_keys = take(static_cast<size_t>(pl->windows) * 8);
+    pl->o_tickets = take(mp_batch_plan::NQ * sizeof(unsigned));
+    if (pl->zwindows > 0) {
+        const size_t Z = static_cast<size_t>(pl->zwindows);
+        pl->o_mu = take(Z * 8);
+        pl->o_S = take(Z * 8);
+        pl->o_flat = take(Z);
+        pl->o_df = take(Z * 4);
+        pl->o_dg = take(Z * 4);
+        pl->o_inv = take(Z * 4);
+        pl->o_muh = take(Z * 4);
+        pl->o_mul = take(Z * 4);
+    }
+    pl->ws_bytes = off;
+
+    // device side
+    cudaError_t e = cudaGetDevice(&pl->device);
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_series, sizeof(mpk::BatchSeries) * pl->S);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_wstart, sizeof(long long) * (pl->S + 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(pl->d_series, pl->series.data(), sizeof(mpk::BatchSeries) * pl->S, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(pl->d_wstart, pl->w_start.data(), sizeof(long long) * (pl->S + 1), cudaMemcpyHostToDevice);
+    for (int qi = 0; qi < mp_batch_plan::NQ && e == cudaSuccess; ++qi) {
+        if (pl->tiles[qi].empty()) continue;
+        const size_t bytes = sizeof(mpk::BatchTile) * pl->tiles[qi].size();
+        e = cudaMalloc(&pl->d_tiles[qi], bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(pl->d_tiles[qi], pl->tiles[qi].data(), bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) break;
+        if (qi == mp_batch_plan::Q_FAST2) {
+            e = cudaFuncSetAttribute(mpk::sweep2_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(pl->smem[qi]));
+            if (e == cudaSuccess) batch_grid(pl, qi, mpk::sweep2_batch_kernel, mpk::V2_NT, sms);
+        } else if (qi == mp_batch_plan::Q_Z) {
+            e = cudaFuncSetAttribute(mpk::sweepz_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(pl->smem[qi]));
+            if (e == cudaSuccess) batch_grid(pl, qi, mpk::sweepz_batch_kernel, mpk::Z_NT, sms);
+        } else {
+            e = gen_dispatch_attr(pl, qi, qi == mp_batch_plan::Q_GEN2 ? mpk::K_P2 : pl->genp_kind, sms);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        batch_free(pl);
+        return cuda_fail(e, "creating the batch plan");
+    }
+    // the tile lists stay on the host only as long as the plan (for mp_batch_tiles)
+    *plan = pl;
+    if (ws_bytes) *ws_bytes = pl->ws_bytes;
+    return MP_OK;
+}
+
+mp_status mp_batch_run(mp_batch_plan *plan, const void *T, double *P, int64_t *I, void *ws, size_t ws_bytes,
+                       void *stream) {
+    g_err[0] = 0;
+    if (!plan) return fail(MP_ERR_INVALID_ARG, "plan is NULL");
+    if (!T || !P || !I) return fail(MP_ERR_INVALID_ARG, "NULL T, P or I");
+    if (!aligned(T, 4) || !aligned(P, 8) || !aligned(I, 8)) return fail(MP_ERR_INVALID_ARG, "misaligned T, P or I");
+    if (!ws) return fail(MP_ERR_WORKSPACE, "workspace is NULL (need %zu bytes)", plan->ws_bytes);
+    if (!aligned(ws, ALIGN)) return fail(MP_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+    if (ws_bytes < plan->ws_bytes)
+        return fail(MP_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, plan->ws_bytes);
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != plan->device) return fail(MP_ERR_INVALID_ARG, "plan made on device %d, current %d", plan->device, dev);
+    cudaGetLastError();
+    if (!plan->exec || plan->g_T != T || plan->g_P != P || plan->g_I != I || plan->g_ws != ws) {
+        mp_status s = batch_build_graph(plan, T, P, I, ws);
+        if (s != MP_OK) return s;
+    }
+    e = cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    counted(plan->nodes);
+    return MP_OK;
+}
+
+int64_t mp_batch_windows(const mp_batch_plan *plan) { return plan ? plan->windows : -1; }
+
+int64_t mp_batch_tiles(const mp_batch_plan *plan) {
+    if (!plan) return -1;
+    int64_t t = 0;
+    for (const auto &q : plan->tiles) t += static_cast<int64_t>(q.size());
+    return t;
+}
+
+mp_status mp_batch_plan_destroy(mp_batch_plan *plan) {
+    batch_free(plan);
     return MP_OK;
 }
 

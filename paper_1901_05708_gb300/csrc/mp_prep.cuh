@@ -99,25 +99,31 @@ __global__ void __launch_bounds__(PREP_NT) fill_u64_kernel(unsigned long long *_
 // Two passes per window in FP64 over the (shifted) FP64 series x.  One
 // thread per window; neighbouring threads read overlapping windows through
 // the cache.  O(n m) FP64 work, a small share of the sweep for m <= 512.
+// One window (X = double, or float for an FP32 series read directly).
+template <typename X>
+__device__ __forceinline__ void window_stats_at(const X *__restrict__ x, long long i, int m, double &mean,
+                                                double &S, unsigned char &flat) {
+    double a = 0.0;
+    for (int l = 0; l < m; ++l) a += static_cast<double>(x[i + l]);
+    mean = a / m;
+    double q = 0.0, r = 0.0;
+    for (int l = 0; l < m; ++l) {
+        const double v = static_cast<double>(x[i + l]);
+        const double d = v - mean;
+        q = fma(d, d, q);
+        r = fma(v, v, r);
+    }
+    S = q;
+    flat = q <= 0x1p-40 * r;
+}
+
 __global__ void __launch_bounds__(PREP_NT) window_stats_kernel(const double *__restrict__ x, long long N, int m,
                                                                double *__restrict__ mu,
                                                                double *__restrict__ S,
                                                                unsigned char *__restrict__ flat) {
     for (long long i = blockIdx.x * (long long)PREP_NT + threadIdx.x; i < N;
-         i += (long long)gridDim.x * PREP_NT) {
-        double a = 0.0;
-        for (int l = 0; l < m; ++l) a += x[i + l];
-        const double mean = a / m;
-        double q = 0.0, r = 0.0;
-        for (int l = 0; l < m; ++l) {
-            const double d = x[i + l] - mean;
-            q = fma(d, d, q);
-            r = fma(x[i + l], x[i + l], r);
-        }
-        mu[i] = mean;
-        S[i] = q;
-        flat[i] = q <= 0x1p-40 * r;
-    }
+         i += (long long)gridDim.x * PREP_NT)
+        window_stats_at(x, i, m, mu[i], S[i], flat[i]);
 }
 
 // FP32 operands of the centred-covariance sweep (derived in FP64):
@@ -127,6 +133,27 @@ __global__ void __launch_bounds__(PREP_NT) window_stats_kernel(const double *__r
 //                          and never wins a minimum)
 // so that cov_{i+1,j+1} = cov_{i,j} + df_i dg_j + df_j dg_i and
 // rho_{i,j} = cov_{i,j} inv_i inv_j (Lemma 3 with A = m mu, C = cov + m mu_i mu_j).
+template <typename X>
+__device__ __forceinline__ void znorm_operands_at(const X *__restrict__ x, long long i, long long N, int m,
+                                                  const double *__restrict__ mu, const double *__restrict__ S,
+                                                  const unsigned char *__restrict__ flat, double shift,
+                                                  float *__restrict__ df, float *__restrict__ dg,
+                                                  float *__restrict__ inv, float *__restrict__ muf,
+                                                  float *__restrict__ mul) {
+    inv[i] = flat[i] ? __int_as_float(0x7fc00000) : static_cast<float>(1.0 / sqrt(S[i]));
+    const double ms = mu[i] - shift;
+    muf[i] = static_cast<float>(ms);
+    if (mul) mul[i] = static_cast<float>(ms - static_cast<double>(muf[i]));  // float-float mean
+    if (i + 1 < N) {
+        const double xe = static_cast<double>(x[i + m]), xl = static_cast<double>(x[i]);
+        df[i] = static_cast<float>(0.5 * (xe - xl));
+        dg[i] = static_cast<float>((xe - mu[i + 1]) + (xl - mu[i]));
+    } else {
+        df[i] = 0.f;
+        dg[i] = 0.f;
+    }
+}
+
 __global__ void __launch_bounds__(PREP_NT) znorm_operands_kernel(const double *__restrict__ x, long long N, int m,
                                                                  const double *__restrict__ mu,
                                                                  const double *__restrict__ S,
@@ -140,17 +167,7 @@ __global__ void __launch_bounds__(PREP_NT) znorm_operands_kernel(const double *_
     for (long long i = blockIdx.x * (long long)PREP_NT + threadIdx.x; i < padded;
          i += (long long)gridDim.x * PREP_NT) {
         if (i < N) {
-            inv[i] = flat[i] ? __int_as_float(0x7fc00000) : static_cast<float>(1.0 / sqrt(S[i]));
-            const double ms = mu[i] - shift;
-            muf[i] = static_cast<float>(ms);
-            if (mul) mul[i] = static_cast<float>(ms - static_cast<double>(muf[i]));  // float-float mean
-            if (i + 1 < N) {
-                df[i] = static_cast<float>(0.5 * (x[i + m] - x[i]));
-                dg[i] = static_cast<float>((x[i + m] - mu[i + 1]) + (x[i] - mu[i]));
-            } else {
-                df[i] = 0.f;
-                dg[i] = 0.f;
-            }
+            znorm_operands_at(x, i, N, m, mu, S, flat, shift, df, dg, inv, muf, mul);
         } else {
             inv[i] = __int_as_float(0x7fc00000);
             muf[i] = 0.f;
@@ -164,10 +181,11 @@ __global__ void __launch_bounds__(PREP_NT) znorm_operands_kernel(const double *_
 // ---- a6: finalize ----------------------------------------------------------------
 enum { FIN_EUCLID = 0, FIN_PNORM = 1, FIN_ZNORM = 2 };
 
-struct FinalizeArgs {
+template <typename X>
+struct FinalizeArgsT {
     const unsigned long long *keys;  // FP32 sweep keys, or
     const Key128 *keys128;           // FP64 sweep keys
-    const double *x;                 // FP64 series (shifted) for the polish
+    const X *x;                      // the series for the polish (FP64, or FP32 read as FP64)
     const double *mu, *S;            // z-norm stats (FP64)
     long long N;
     int m;
@@ -177,6 +195,7 @@ struct FinalizeArgs {
     double *P;
     long long *I;
 };
+using FinalizeArgs = FinalizeArgsT<double>;
 
 __device__ __forceinline__ double pow_abs(double v, double p) {
     v = fabs(v);
@@ -187,28 +206,30 @@ __device__ __forceinline__ double pow_abs(double v, double p) {
 }
 
 // d(i, j) from the definitions (Sec. 2) in FP64.
-__device__ double exact_score(const FinalizeArgs &a, long long i, long long j) {
-    const double *xi = a.x + i, *xj = a.x + j;
+template <typename X>
+__device__ double exact_score(const FinalizeArgsT<X> &a, long long i, long long j) {
+    const X *xi = a.x + i, *xj = a.x + j;
     double acc = 0.0;
     if (a.dist == FIN_EUCLID) {
         for (int l = 0; l < a.m; ++l) {
-            const double d = xi[l] - xj[l];
+            const double d = static_cast<double>(xi[l]) - static_cast<double>(xj[l]);
             acc = fma(d, d, acc);
         }
     } else if (a.dist == FIN_PNORM) {
-        for (int l = 0; l < a.m; ++l) acc += pow_abs(xi[l] - xj[l], a.p);
+        for (int l = 0; l < a.m; ++l) acc += pow_abs(static_cast<double>(xi[l]) - static_cast<double>(xj[l]), a.p);
     } else {
         const double mi = a.mu[i], mj = a.mu[j];
         const double si = 1.0 / sqrt(a.S[i] / a.m), sj = 1.0 / sqrt(a.S[j] / a.m);
         for (int l = 0; l < a.m; ++l) {
-            const double d = (xi[l] - mi) * si - (xj[l] - mj) * sj;
+            const double d = (static_cast<double>(xi[l]) - mi) * si - (static_cast<double>(xj[l]) - mj) * sj;
             acc = fma(d, d, acc);
         }
     }
     return acc;
 }
 
-__device__ __forceinline__ double finish_score(const FinalizeArgs &a, double s) {
+template <typename X>
+__device__ __forceinline__ double finish_score(const FinalizeArgsT<X> &a, double s) {
     if (s < 0) s = 0;
     if (a.dist == FIN_PNORM) {
         if (a.p == 1.0) return s;
@@ -218,38 +239,43 @@ __device__ __forceinline__ double finish_score(const FinalizeArgs &a, double s) 
     return sqrt(s);
 }
 
+// Window x: key -> I[x]; P[x] from the sweep value or, polished, from d(x, I[x]).
+template <typename X>
+__device__ __forceinline__ void finalize_at(const FinalizeArgsT<X> &a, long long x) {
+    unsigned long long lo;
+    double sweep_score;
+    bool none;
+    if (a.keys) {
+        const unsigned long long key = a.keys[x];
+        none = key == KEY_NONE;
+        lo = key & 0xffffffffull;
+        const float v = __uint_as_float(static_cast<unsigned>(key >> 32));
+        // z-norm keys hold 1 - rho; DZ^2 = 2m(1 - rho) (Lemma 3)
+        sweep_score = a.dist == FIN_ZNORM ? 2.0 * a.m * static_cast<double>(v) : static_cast<double>(v);
+    } else {
+        const Key128 key = a.keys128[x];
+        none = key.hi == KEY_NONE;
+        lo = key.lo;
+        const double v = __longlong_as_double(static_cast<long long>(key.hi));
+        sweep_score = a.dist == FIN_ZNORM ? 2.0 * a.m * v : v;
+    }
+    if (none) {
+        a.P[x] = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+        a.I[x] = -1;
+        return;
+    }
+    const long long k = static_cast<long long>(lo >> 1);
+    const long long j = (lo & 1) ? x + k : x - k;
+    a.I[x] = j;
+    double s = a.polish ? exact_score(a, x, j) : sweep_score;
+    if (a.dist == FIN_ZNORM) s = fmin(fmax(s, 0.0), 4.0 * a.m);
+    a.P[x] = finish_score(a, s);
+}
+
 __global__ void __launch_bounds__(PREP_NT) finalize_kernel(FinalizeArgs a) {
     for (long long x = blockIdx.x * (long long)PREP_NT + threadIdx.x; x < a.N;
-         x += (long long)gridDim.x * PREP_NT) {
-        unsigned long long lo;
-        double sweep_score;
-        bool none;
-        if (a.keys) {
-            const unsigned long long key = a.keys[x];
-            none = key == KEY_NONE;
-            lo = key & 0xffffffffull;
-            const float v = __uint_as_float(static_cast<unsigned>(key >> 32));
-            // z-norm keys hold 1 - rho; DZ^2 = 2m(1 - rho) (Lemma 3)
-            sweep_score = a.dist == FIN_ZNORM ? 2.0 * a.m * static_cast<double>(v) : static_cast<double>(v);
-        } else {
-            const Key128 key = a.keys128[x];
-            none = key.hi == KEY_NONE;
-            lo = key.lo;
-            const double v = __longlong_as_double(static_cast<long long>(key.hi));
-            sweep_score = a.dist == FIN_ZNORM ? 2.0 * a.m * v : v;
-        }
-        if (none) {
-            a.P[x] = __longlong_as_double(0x7ff0000000000000ll);  // +inf
-            a.I[x] = -1;
-            continue;
-        }
-        const long long k = static_cast<long long>(lo >> 1);
-        const long long j = (lo & 1) ? x + k : x - k;
-        a.I[x] = j;
-        double s = a.polish ? exact_score(a, x, j) : sweep_score;
-        if (a.dist == FIN_ZNORM) s = fmin(fmax(s, 0.0), 4.0 * a.m);
-        a.P[x] = finish_score(a, s);
-    }
+         x += (long long)gridDim.x * PREP_NT)
+        finalize_at(a, x);
 }
 
 }  // namespace mpk

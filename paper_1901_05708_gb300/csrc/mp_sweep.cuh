@@ -25,8 +25,9 @@
 // are reduced over the D slots of a row; column keys are reduced in D
 // rotating registers, since column c = i + k receives slot d from row
 // c - k0 - tD - d.  A reduced key that can beat the tile's cached best
-// (shared-memory thresholds loaded from the global keys) goes to a global
-// 64-bit atomicMin.
+// (shared-memory thresholds loaded from the global keys) lowers that
+// threshold and, if it was still the tile's best, goes to a global 64-bit
+// atomicMin.
 //
 // Shared-memory layout.  The j-side series values of the entering and the
 // leaving terms are kept in two copies offset by m, so that a thread's
@@ -104,18 +105,12 @@ __device__ __forceinline__ unsigned key_value(int key) {
 // padded position of x in a j-side copy: one pad word after every D words
 __host__ __device__ __forceinline__ int jpos(int x) { return x + x / SW_D; }
 
+// One tile (band, rt) of one problem.  Every thread of the CTA calls it; it
+// synchronises once (after staging) and may return early per thread after that.
 template <int KIND, bool SPLIT>
-__global__ void __launch_bounds__(SW_NT, 2) sweep_kernel(const SweepArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void sweep_tile(const SweepArgs &a, long long band, long long rt, unsigned char *smem) {
     const int R = a.R, m = a.m, B = a.B, Q = a.Q, RL = a.RL;
     const int tid = threadIdx.x;
-
-    long long band, rt;
-    decode_tile(a, blockIdx.x, band, rt);
-    if (rt < 0 || rt >= a.C - static_cast<long long>(a.q) * band) {  // cannot happen; never touch memory
-        if (tid == 0) atomicOr(&mp_device_error, ERR_BAD_TILE);
-        return;
-    }
     const long long k0 = a.k_first + band * SW_KW;
     const long long r0 = rt * R;
 
@@ -309,8 +304,7 @@ __global__ void __launch_bounds__(SW_NT, 2) sweep_kernel(const SweepArgs a) {
                     const unsigned wmin = __reduce_min_sync(__activemask(), v);
                     if (v == wmin) {
                         const long long k = kt + (rk & (SW_D - 1));
-                        atomicMin(&a.keys[r0 + u], make_key(v, k, 1));
-                        atomicMin(&thr_r[u], v);
+                        if (v <= atomicMin(&thr_r[u], v)) atomicMin(&a.keys[r0 + u], make_key(v, k, 1));
                     }
                 }
             }
@@ -323,8 +317,7 @@ __global__ void __launch_bounds__(SW_NT, 2) sweep_kernel(const SweepArgs a) {
                     const int cl = jb + u;  // local column index
                     if (v <= thr_c[cl]) {
                         const long long k = kt + (ck & (SW_D - 1));
-                        atomicMin(&a.keys[r0 + kt + u], make_key(v, k, 0));
-                        atomicMin(&thr_c[cl], v);
+                        if (v <= atomicMin(&thr_c[cl], v)) atomicMin(&a.keys[r0 + kt + u], make_key(v, k, 0));
                     }
                 }
             }
@@ -342,10 +335,21 @@ __global__ void __launch_bounds__(SW_NT, 2) sweep_kernel(const SweepArgs a) {
         const unsigned v = key_value(ck);
         if (v <= thr_c[cl]) {
             const long long k = kt + (ck & (SW_D - 1));
-            atomicMin(&a.keys[r0 + kt + ulast + delta], make_key(v, k, 0));
-            atomicMin(&thr_c[cl], v);
+            if (v <= atomicMin(&thr_c[cl], v)) atomicMin(&a.keys[r0 + kt + ulast + delta], make_key(v, k, 0));
         }
     }
+}
+
+template <int KIND, bool SPLIT>
+__global__ void __launch_bounds__(SW_NT, 2) sweep_kernel(const SweepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    long long band, rt;
+    decode_tile(a, blockIdx.x, band, rt);
+    if (rt < 0 || rt >= a.C - static_cast<long long>(a.q) * band) {  // cannot happen; never touch memory
+        if (threadIdx.x == 0) atomicOr(&mp_device_error, ERR_BAD_TILE);
+        return;
+    }
+    sweep_tile<KIND, SPLIT>(a, band, rt, smem);
 }
 
 // Rows held by the leaving copies (they also serve the anchor, which needs m + 1).

@@ -163,13 +163,19 @@ __device__ __forceinline__ void v2_tag8(float *t, const float2 *s, bool sb, int 
 // decides the tie.
 __device__ __forceinline__ float v2_thr_form(unsigned value_bits) { return __uint_as_float(value_bits | (V2_D - 1)); }
 
-// A tagged minimum that passed its threshold: global key + tile threshold.
+// A tagged minimum that passed its threshold: tile threshold first, then the
+// global key only if this candidate still matches or beats the tile's best
+// (the threshold it replaced).  When all threads of a tile offer a candidate
+// for the same row at once (thresholds still open early in a sweep), about
+// ln(threads) of them reach the global atomic instead of every one.  Equal
+// values still go out: a smaller k must win the key.
 __device__ __forceinline__ void v2_emit(unsigned long long *keys, float *thr, int thr_idx, long long target,
                                         float tagged, long long kt, int right) {
     const int bits = __float_as_int(tagged);
     const unsigned v = bits < 0 ? 0u : static_cast<unsigned>(bits & ~(V2_D - 1));
-    atomicMin(&keys[target], make_key(v, kt + (bits & (V2_D - 1)), right));
-    atomicMin(reinterpret_cast<int *>(thr) + thr_idx, static_cast<int>(v | (V2_D - 1)));
+    const int t = static_cast<int>(v | (V2_D - 1));
+    const int old = atomicMin(reinterpret_cast<int *>(thr) + thr_idx, t);
+    if (t <= old) atomicMin(&keys[target], make_key(v, kt + (bits & (V2_D - 1)), right));
 }
 
 // 1 if any of the eight tests a_i <= b_i holds: eight compares chained into
@@ -202,16 +208,12 @@ __device__ __forceinline__ float2 v2_sub(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, one rounding
 }
 
-__global__ void __launch_bounds__(V2_NT, 2) sweep2_kernel(const Sweep2Args a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+// One tile (band, rt) of one problem.  Every thread of the CTA calls it; it
+// synchronises once (after staging) and may return early per thread after that.
+__device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band, long long rt,
+                                            unsigned char *smem) {
     const int m = a.m, B = a.B, Q = a.Q;
     const int tid = threadIdx.x;
-
-    long long band, rt;
-    if (!v2_decode(a, blockIdx.x, band, rt)) {
-        if (tid == 0) atomicOr(&mp_device_error, ERR_BAD_TILE);
-        return;
-    }
     const long long k0 = a.k_first + band * V2_KW;
     const long long r0 = rt * V2_R;
     const long long Lb = a.L - band * V2_KW;  // rows where diagonal k0 is valid
@@ -467,6 +469,16 @@ __global__ void __launch_bounds__(V2_NT, 2) sweep2_kernel(const Sweep2Args a) {
         if (cb[sl] != NONE && cb[sl] <= thr_c[col_idx(uc, 1)])
             v2_emit(a.keys, thr_c, col_idx(uc, 1), col_tgt(uc, 1), cb[sl], kt, 0);
     }
+}
+
+__global__ void __launch_bounds__(V2_NT, 2) sweep2_kernel(const Sweep2Args a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    long long band, rt;
+    if (!v2_decode(a, blockIdx.x, band, rt)) {
+        if (threadIdx.x == 0) atomicOr(&mp_device_error, ERR_BAD_TILE);
+        return;
+    }
+    sweep2_tile(a, band, rt, smem);
 }
 
 }  // namespace mpk

@@ -73,16 +73,12 @@ inline size_t sweepz_smem_bytes() {
 
 __device__ __forceinline__ float2 z_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
-__global__ void __launch_bounds__(Z_NT, 2) sweepz_kernel(const SweepZArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+// One tile (band, rt) of one problem; every thread of the CTA calls it (the
+// chunk loop synchronises the whole CTA).
+__device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band, long long rt,
+                                            unsigned char *smem) {
     const int m = a.m;
     const int tid = threadIdx.x;
-
-    long long band, rt;
-    if (!z_decode(a, blockIdx.x, band, rt)) {
-        if (tid == 0) atomicOr(&mp_device_error, ERR_BAD_TILE);
-        return;
-    }
     const long long k0 = a.k_first + band * Z_KW;
     const long long r0 = rt * Z_S;
     const long long Lb = a.L - band * Z_KW;
@@ -355,6 +351,16 @@ __global__ void __launch_bounds__(Z_NT, 2) sweepz_kernel(const SweepZArgs a) {
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(Z_NT, 2) sweepz_kernel(const SweepZArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    long long band, rt;
+    if (!z_decode(a, blockIdx.x, band, rt)) {
+        if (threadIdx.x == 0) atomicOr(&mp_device_error, ERR_BAD_TILE);
+        return;
+    }
+    sweepz_tile(a, band, rt, smem);
 }
 
 }  // namespace mpk

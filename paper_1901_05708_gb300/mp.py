@@ -8,6 +8,8 @@ be loaded, every call raises.
     P, I = aamp(T, m, excl)            # pure Euclidean   (Algorithm 1)
     P, I = pnorm(T, m, excl, p)        # p-norm           (Algorithm 3)
     P, I = acamp(T, m, excl)           # z-normalised     (Algorithm 2)
+    plan = BatchPlan(lengths, ms, dists, excls)   # many series, one graph
+    P, I = plan.run(T_concat)
 
 T is a 1-D float32/float64 CUDA tensor; P (float64) and I (int64) come back
 on the same device.  Calls are asynchronous on the current torch stream.
@@ -28,7 +30,8 @@ MP_DIST_EUCLID, MP_DIST_PNORM, MP_DIST_ZNORM = 0, 1, 2
 
 EXPORTS = ("mp_options_default", "mp_workspace_size", "mp_aamp", "mp_pnorm", "mp_acamp",
            "mp_sync_status", "mp_last_error", "mp_status_string", "mp_version", "mp_launch_count",
-           "mp_set_sweep_events")
+           "mp_set_sweep_events", "mp_aamp_noalloc", "mp_batch_plan_create", "mp_batch_run",
+           "mp_batch_windows", "mp_batch_tiles", "mp_batch_plan_destroy")
 
 
 class MPError(RuntimeError):
@@ -46,6 +49,13 @@ class Options(ctypes.Structure):
                 ("reanchor", ctypes.c_int32), ("polish", ctypes.c_int32),
                 ("reserved0", ctypes.c_int32), ("k_begin", ctypes.c_int64),
                 ("k_end", ctypes.c_int64)]
+
+
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("num_series", ctypes.c_int32),
+                ("t_offsets", ctypes.POINTER(ctypes.c_int64)), ("m", ctypes.POINTER(ctypes.c_int32)),
+                ("dist", ctypes.POINTER(ctypes.c_uint8)), ("excl", ctypes.POINTER(ctypes.c_int64)),
+                ("p", ctypes.c_double), ("dtype", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -83,6 +93,19 @@ def load(path: str | None = None):
         lib.mp_launch_count.restype = ctypes.c_uint64
         lib.mp_set_sweep_events.argtypes = [vp, vp]
         lib.mp_set_sweep_events.restype = ctypes.c_int
+        lib.mp_aamp_noalloc.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, vp, opt_p, vp]
+        lib.mp_aamp_noalloc.restype = ctypes.c_int
+        lib.mp_batch_plan_create.argtypes = [ctypes.POINTER(BatchDesc), opt_p, ctypes.POINTER(vp),
+                                             ctypes.POINTER(sz)]
+        lib.mp_batch_plan_create.restype = ctypes.c_int
+        lib.mp_batch_run.argtypes = [vp, vp, vp, vp, vp, sz, vp]
+        lib.mp_batch_run.restype = ctypes.c_int
+        lib.mp_batch_windows.argtypes = [vp]
+        lib.mp_batch_windows.restype = i64
+        lib.mp_batch_tiles.argtypes = [vp]
+        lib.mp_batch_tiles.restype = i64
+        lib.mp_batch_plan_destroy.argtypes = [vp]
+        lib.mp_batch_plan_destroy.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -191,3 +214,101 @@ def profile(T, m, excl, dist="euclid", p=2.0, **kw):
     if dist in ("pnorm", MP_DIST_PNORM):
         return pnorm(T, m, excl, p, **kw)
     return acamp(T, m, excl, **kw)
+
+
+_DIST_CODES = {"euclid": MP_DIST_EUCLID, "pnorm": MP_DIST_PNORM, "znorm": MP_DIST_ZNORM}
+
+
+def batch_desc(lengths, m, dist, excl, p: float = 2.0):
+    """An mp_batch_desc over host arrays (kept alive in the returned tuple)."""
+    import numpy as np
+    lengths = np.asarray(lengths, dtype=np.int64)
+    S = lengths.size
+    offs = np.zeros(S + 1, dtype=np.int64)
+    np.cumsum(lengths, out=offs[1:])
+    ms = np.ascontiguousarray(np.broadcast_to(np.asarray(m, dtype=np.int32), (S,)))
+    d = [_DIST_CODES.get(x, x) if isinstance(x, str) else int(x) for x in np.atleast_1d(dist)]
+    ds = np.ascontiguousarray(np.broadcast_to(np.asarray(d, dtype=np.uint8), (S,)))
+    ex = np.ascontiguousarray(np.broadcast_to(np.asarray(excl, dtype=np.int64), (S,)))
+    desc = BatchDesc()
+    desc.struct_size = ctypes.sizeof(BatchDesc)
+    desc.num_series = S
+    desc.t_offsets = offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    desc.m = ms.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    desc.dist = ds.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    desc.excl = ex.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    desc.p = float(p)
+    desc.dtype = MP_F32
+    return desc, (offs, ms, ds, ex)
+
+
+class BatchPlan:
+    """Matrix profiles of many float32 series in one graph launch (mp_batch_*).
+
+    lengths[s], m[s], dist[s] ('euclid' | 'pnorm' | 'znorm' or mp_dist codes)
+    and excl[s] describe series s; p is the exponent of every p-norm series.
+    run(T) takes the series concatenated in one float32 CUDA tensor and
+    returns (P, I) concatenated: series s at out_offsets[s] .. out_offsets[s+1],
+    I within the series.  The plan keeps its workspace, so that repeated runs
+    with the same output buffers replay the same graph."""
+
+    def __init__(self, lengths, m, dist, excl, p: float = 2.0, polish: bool = True, device=None):
+        import numpy as np
+        lib = load()
+        self._desc, keep = batch_desc(lengths, m, dist, excl, p)
+        offs, ms, _, _ = keep
+        self.t_offsets = offs
+        N = (offs[1:] - offs[:-1]) - ms + 1
+        self.out_offsets = np.zeros(N.size + 1, dtype=np.int64)
+        np.cumsum(N, out=self.out_offsets[1:])
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index)
+        opt = options(polish=polish)
+        h = ctypes.c_void_p()
+        nbytes = ctypes.c_size_t()
+        with torch.cuda.device(self.device):
+            _check(lib.mp_batch_plan_create(ctypes.byref(self._desc), ctypes.byref(opt), ctypes.byref(h),
+                                            ctypes.byref(nbytes)))
+        self._h = h
+        self.windows = int(lib.mp_batch_windows(h))
+        self.tiles = int(lib.mp_batch_tiles(h))
+        self.ws_bytes = int(nbytes.value)
+        self._ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=self.device)
+
+    def run(self, T: torch.Tensor, out=None, stream=None):
+        if self._h is None:
+            raise RuntimeError("plan is closed")
+        if not isinstance(T, torch.Tensor) or not T.is_cuda or T.dtype != torch.float32 or T.dim() != 1:
+            raise TypeError("T must be a 1-D float32 CUDA tensor")
+        if T.numel() != int(self.t_offsets[-1]):
+            raise ValueError(f"T has {T.numel()} samples, the plan {int(self.t_offsets[-1])}")
+        T = T.contiguous()
+        if out is None:
+            P = torch.empty(self.windows, dtype=torch.float64, device=T.device)
+            I = torch.empty(self.windows, dtype=torch.int64, device=T.device)
+        else:
+            P, I = out
+        s = stream if stream is not None else torch.cuda.current_stream(T.device)
+        _check(load().mp_batch_run(self._h, ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(P.data_ptr()),
+                                   ctypes.c_void_p(I.data_ptr()), ctypes.c_void_p(self._ws.data_ptr()),
+                                   self._ws.numel(), ctypes.c_void_p(s.cuda_stream)))
+        return P, I
+
+    def close(self):
+        """Free the plan (after waiting for the device: a run may still be in flight)."""
+        if getattr(self, "_h", None) is not None:
+            torch.cuda.synchronize(self.device)
+            load().mp_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -88,6 +88,50 @@ def test_argument_checks_need_no_gpu(lib):
                         None, vp(0)) == E.MP_ERR_INVALID_ARG
 
 
+def test_batch_checks_need_no_gpu(lib):
+    """mp_batch_plan_create validates the whole description before any CUDA call."""
+    E = mp
+
+    def create(lengths=(100, 50), m=(10, 8), dist=(0, 2), excl=(2, 2), p=2.0, dtype=None, opt=None,
+               **patch):
+        desc, keep = mp.batch_desc(lengths, m, dist, excl, p)
+        if dtype is not None:
+            desc.dtype = dtype
+        for k, v in patch.items():
+            setattr(desc, k, v)
+        h = ctypes.c_void_p()
+        nb = ctypes.c_size_t()
+        st = lib.mp_batch_plan_create(ctypes.byref(desc), ctypes.byref(opt) if opt else None,
+                                      ctypes.byref(h), ctypes.byref(nb))
+        assert not h.value  # nothing was created
+        return st
+
+    assert create(num_series=0) == E.MP_ERR_INVALID_ARG
+    assert create(struct_size=8) == E.MP_ERR_INVALID_ARG
+    assert create(m=(10, 51)) == E.MP_ERR_INVALID_ARG           # m > n
+    assert create(m=(0, 8)) == E.MP_ERR_INVALID_ARG
+    assert create(lengths=(100, 0)) == E.MP_ERR_INVALID_ARG     # empty series
+    assert create(dist=(0, 7)) == E.MP_ERR_INVALID_ARG
+    assert create(m=(10, 1)) == E.MP_ERR_INVALID_ARG            # z-normalised with m = 1
+    assert create(excl=(-1, 2)) == E.MP_ERR_INVALID_ARG
+    assert create(dist=(1, 0), p=0.5) == E.MP_ERR_INVALID_ARG   # p < 1 for a p-norm series
+    assert create(dtype=mp.MP_F64) == E.MP_ERR_UNSUPPORTED
+    assert create(dtype=9) == E.MP_ERR_INVALID_ARG
+    o = mp.Options()
+    lib.mp_options_default(ctypes.byref(o))
+    o.precision = mp.MP_PREC_FP64
+    assert create(opt=o) == E.MP_ERR_UNSUPPORTED
+    lib.mp_options_default(ctypes.byref(o))
+    o.k_end = 5
+    assert create(opt=o) == E.MP_ERR_UNSUPPORTED
+    assert b"diagonal" in lib.mp_last_error()
+    h = ctypes.c_void_p()
+    assert lib.mp_batch_plan_create(None, None, ctypes.byref(h), None) == E.MP_ERR_INVALID_ARG
+    assert lib.mp_batch_run(None, None, None, None, None, 0, None) == E.MP_ERR_INVALID_ARG
+    assert lib.mp_batch_windows(None) == -1 and lib.mp_batch_tiles(None) == -1
+    assert lib.mp_batch_plan_destroy(None) == E.MP_OK
+
+
 def test_binding_refuses_cpu_tensors(lib):
     torch = pytest.importorskip("torch")
     with pytest.raises(TypeError):
