@@ -220,7 +220,7 @@ mp_status launch_sweep_t(const mpk::SweepArgs &a, size_t smem, cudaStream_t st) 
 bool fast_path_ok(const Problem &pb) {
     const bool euclid = pb.dist == MP_DIST_EUCLID || (pb.dist == MP_DIST_PNORM && pb.p == 2.0);
     return euclid && pb.dtype == MP_F32 && pb.m % 32 == 0 && pb.opt.reanchor == 0 &&
-           mpk::sweep2_smem_bytes(pb.m, mpk::V2_QMAX) <= 110 * 1024 && !getenv_generic();
+           mpk::sweep2_smem_bytes(pb.m, mpk::V2_QMAX) <= mpk::V2_SMEM_MAX && !getenv_generic();
 }
 
 mp_status run_sweep2(const Problem &pb, const Layout &L, char *ws, cudaStream_t st) {
@@ -830,7 +830,7 @@ mp_status mp_batch_plan_create(const mp_batch_desc *desc, const mp_options *opt,
             pl->zwindows += b.N;
             qi = mp_batch_plan::Q_Z;
             batch_tiles(q[qi], si, L, mpk::Z_KW, mpk::Z_S);
-        } else if (p2 && b.m % 32 == 0 && mpk::sweep2_smem_bytes(b.m, mpk::V2_QMAX) <= 110 * 1024) {
+        } else if (p2 && b.m % 32 == 0 && mpk::sweep2_smem_bytes(b.m, mpk::V2_QMAX) <= mpk::V2_SMEM_MAX) {
             qi = mp_batch_plan::Q_FAST2;
             batch_tiles(q[qi], si, L, mpk::V2_KW, mpk::V2_R);
         } else {

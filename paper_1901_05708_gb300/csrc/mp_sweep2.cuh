@@ -40,12 +40,14 @@
 
 namespace mpk {
 
-constexpr int V2_NT = 128;             // threads per CTA
+constexpr int V2_NT = 192;             // threads per CTA (two CTAs, 12 warps, per SM)
 constexpr int V2_D = 8;                // diagonals per thread
 constexpr int V2_KW = V2_NT * V2_D;    // diagonals per band
 constexpr int V2_H = 1024;             // rows per stream
 constexpr int V2_R = 2 * V2_H;         // rows per tile
 constexpr int V2_QMAX = 4;             // ring blocks per diagonal
+// shared memory of one CTA such that two fit on an SM (228 KB, 1 KB reserved per CTA)
+constexpr size_t V2_SMEM_MAX = 113 * 1024;
 
 struct Sweep2Args {
     const float *t;             // FP32 series, n values
