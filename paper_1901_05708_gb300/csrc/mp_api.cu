@@ -214,13 +214,32 @@ mp_status launch_sweep_t(const mpk::SweepArgs &a, size_t smem, cudaStream_t st) 
     return MP_OK;
 }
 
-// Fast Euclidean path (two row streams, f32x2 arithmetic, lazy argmin): FP32
-// input, m a multiple of 32 (re-anchor every m / 4 rows), default re-anchor
-// interval, shared memory for two CTAs per SM.
+// Exponent kind of a Euclidean / p-norm problem.
+int kind_of(int dist, double p) {
+    if (dist != MP_DIST_PNORM || p == 2.0) return mpk::K_P2;
+    return p == 1.0 ? mpk::K_P1 : p == 3.0 ? mpk::K_P3 : mpk::K_PG;
+}
+
+// Fast two-stream path (f32x2 arithmetic, tagged minima): Euclidean or
+// p-norm with p in {1, 2, 3}, FP32 input, m a multiple of 32 (re-anchor every
+// m / 4 rows), default re-anchor interval, shared memory for two CTAs per SM.
 bool fast_path_ok(const Problem &pb) {
-    const bool euclid = pb.dist == MP_DIST_EUCLID || (pb.dist == MP_DIST_PNORM && pb.p == 2.0);
-    return euclid && pb.dtype == MP_F32 && pb.m % 32 == 0 && pb.opt.reanchor == 0 &&
+    const bool lp = pb.dist == MP_DIST_EUCLID || (pb.dist == MP_DIST_PNORM && kind_of(pb.dist, pb.p) != mpk::K_PG);
+    return lp && pb.dtype == MP_F32 && pb.m % 32 == 0 && pb.opt.reanchor == 0 &&
            mpk::sweep2_smem_bytes(pb.m, mpk::V2_QMAX) <= mpk::V2_SMEM_MAX && !getenv_generic();
+}
+
+template <int KIND>
+mp_status launch_sweep2_t(const mpk::Sweep2Args &a, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(mpk::sweep2_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(sweep2)");
+    {
+        SweepEvents ev(st);
+        mpk::sweep2_kernel<KIND><<<static_cast<unsigned>(a.tiles), mpk::V2_NT, smem, st>>>(a);
+    }
+    counted();
+    return MP_OK;
 }
 
 mp_status run_sweep2(const Problem &pb, const Layout &L, char *ws, cudaStream_t st) {
@@ -240,14 +259,11 @@ mp_status run_sweep2(const Problem &pb, const Layout &L, char *ws, cudaStream_t 
     if (a.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", a.tiles);
     if (a.tiles <= 0) return MP_OK;
     const size_t smem = mpk::sweep2_smem_bytes(a.m, a.Q);
-    cudaError_t e = cudaFuncSetAttribute(mpk::sweep2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(sweep2)");
-    {
-        SweepEvents ev(st);
-        mpk::sweep2_kernel<<<static_cast<unsigned>(a.tiles), mpk::V2_NT, smem, st>>>(a);
+    switch (kind_of(pb.dist, pb.p)) {
+        case mpk::K_P1: return launch_sweep2_t<mpk::K_P1>(a, smem, st);
+        case mpk::K_P3: return launch_sweep2_t<mpk::K_P3>(a, smem, st);
+        default: return launch_sweep2_t<mpk::K_P2>(a, smem, st);
     }
-    counted();
-    return MP_OK;
 }
 
 mp_status run_sweep_f32(const Problem &pb, const Layout &L, char *ws, cudaStream_t st) {
@@ -275,10 +291,7 @@ mp_status run_sweep_f32(const Problem &pb, const Layout &L, char *ws, cudaStream
     const bool split = a.lo != nullptr;
     const size_t smem = mpk::sweep_smem_bytes(a.R, a.m, a.Q, split);
     if (smem > 227 * 1024) return fail(MP_ERR_UNSUPPORTED, "m = %d needs %zu bytes of shared memory", pb.m, smem);
-    int kind = mpk::K_P2;
-    if (pb.dist == MP_DIST_PNORM) {
-        kind = pb.p == 2.0 ? mpk::K_P2 : pb.p == 1.0 ? mpk::K_P1 : pb.p == 3.0 ? mpk::K_P3 : mpk::K_PG;
-    }
+    const int kind = kind_of(pb.dist, pb.p);
     switch (kind * 2 + (split ? 1 : 0)) {
         case 0: return launch_sweep_t<mpk::K_P2, false>(a, smem, st);
         case 1: return launch_sweep_t<mpk::K_P2, true>(a, smem, st);
@@ -569,12 +582,12 @@ mp_status mp_set_sweep_events(void *ev_start, void *ev_end) {
 
 // ---- a7: batches -----------------------------------------------------------------------
 struct mp_batch_plan {
-    enum { Q_FAST2 = 0, Q_Z = 1, Q_GEN2 = 2, Q_GENP = 3, NQ = 4 };
+    enum { Q_FAST2 = 0, Q_Z = 1, Q_GEN2 = 2, Q_GENP = 3, Q_FASTP = 4, NQ = 5 };
     int device = -1;
     int S = 0;
     double p = 2.0;
     int polish = 1;
-    int genp_kind = mpk::K_P2;  // exponent kind of the p-norm generic queue
+    int genp_kind = mpk::K_P2;  // exponent kind of the p-norm queues
     long long windows = 0, zwindows = 0, samples = 0;
     std::vector<mpk::BatchSeries> series;
     std::vector<long long> w_start;
@@ -684,6 +697,14 @@ cudaError_t launch_gen_batch(const mp_batch_plan *pl, const mpk::BatchData &bd, 
 }
 
 template <int KIND>
+cudaError_t fast_batch_attr(mp_batch_plan *pl, int qi, int sms) {
+    cudaError_t e = cudaFuncSetAttribute(mpk::sweep2_batch_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(pl->smem[qi]));
+    if (e == cudaSuccess) batch_grid(pl, qi, mpk::sweep2_batch_kernel<KIND>, mpk::V2_NT, sms);
+    return e;
+}
+
+template <int KIND>
 cudaError_t gen_batch_attr(mp_batch_plan *pl, int qi, int sms) {
     cudaError_t e = cudaFuncSetAttribute(mpk::sweep_batch_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(pl->smem[qi]));
@@ -752,7 +773,11 @@ mp_status batch_build_graph(mp_batch_plan *pl, const void *T, double *P, int64_t
         if (pl->tiles[qi].empty()) continue;
         const mpk::BatchQueue q{pl->d_tiles[qi], static_cast<unsigned>(pl->tiles[qi].size()), tickets + qi};
         if (qi == mp_batch_plan::Q_FAST2)
-            mpk::sweep2_batch_kernel<<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
+            mpk::sweep2_batch_kernel<mpk::K_P2><<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
+        else if (qi == mp_batch_plan::Q_FASTP && pl->genp_kind == mpk::K_P1)
+            mpk::sweep2_batch_kernel<mpk::K_P1><<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
+        else if (qi == mp_batch_plan::Q_FASTP)
+            mpk::sweep2_batch_kernel<mpk::K_P3><<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
         else if (qi == mp_batch_plan::Q_Z)
             mpk::sweepz_batch_kernel<<<pl->grid[qi], mpk::Z_NT, pl->smem[qi], st>>>(bd, q);
         else
@@ -830,8 +855,9 @@ mp_status mp_batch_plan_create(const mp_batch_desc *desc, const mp_options *opt,
             pl->zwindows += b.N;
             qi = mp_batch_plan::Q_Z;
             batch_tiles(q[qi], si, L, mpk::Z_KW, mpk::Z_S);
-        } else if (p2 && b.m % 32 == 0 && mpk::sweep2_smem_bytes(b.m, mpk::V2_QMAX) <= mpk::V2_SMEM_MAX) {
-            qi = mp_batch_plan::Q_FAST2;
+        } else if (b.m % 32 == 0 && mpk::sweep2_smem_bytes(b.m, mpk::V2_QMAX) <= mpk::V2_SMEM_MAX &&
+                   (p2 || pl->genp_kind == mpk::K_P1 || pl->genp_kind == mpk::K_P3)) {
+            qi = p2 ? mp_batch_plan::Q_FAST2 : mp_batch_plan::Q_FASTP;
             batch_tiles(q[qi], si, L, mpk::V2_KW, mpk::V2_R);
         } else {
             qi = p2 ? mp_batch_plan::Q_GEN2 : mp_batch_plan::Q_GENP;
@@ -860,7 +886,8 @@ mp_status mp_batch_plan_create(const mp_batch_desc *desc, const mp_options *opt,
                          [](const auto &a, const auto &b) { return a.first > b.first; });
         pl->tiles[qi].reserve(q[qi].size());
         for (auto &t : q[qi]) pl->tiles[qi].push_back(t.second);
-        if (qi == mp_batch_plan::Q_FAST2) pl->smem[qi] = mpk::sweep2_smem_bytes(std::max(qmax_m[qi], 32), mpk::V2_QMAX);
+        if (qi == mp_batch_plan::Q_FAST2 || qi == mp_batch_plan::Q_FASTP)
+            pl->smem[qi] = mpk::sweep2_smem_bytes(std::max(qmax_m[qi], 32), mpk::V2_QMAX);
         else if (qi == mp_batch_plan::Q_Z) pl->smem[qi] = mpk::sweepz_smem_bytes();
         else pl->smem[qi] = mpk::sweep_smem_bytes(mpk::BATCH_GEN_R, std::max(qmax_m[qi], 1), std::max(qmax_Q[qi], 1), false);
         if (!pl->tiles[qi].empty() && pl->smem[qi] > 227 * 1024) {
@@ -902,10 +929,11 @@ mp_status mp_batch_plan_create(const mp_batch_desc *desc, const mp_options *opt,
         e = cudaMalloc(&pl->d_tiles[qi], bytes);
         if (e == cudaSuccess) e = cudaMemcpy(pl->d_tiles[qi], pl->tiles[qi].data(), bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) break;
-        if (qi == mp_batch_plan::Q_FAST2) {
-            e = cudaFuncSetAttribute(mpk::sweep2_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(pl->smem[qi]));
-            if (e == cudaSuccess) batch_grid(pl, qi, mpk::sweep2_batch_kernel, mpk::V2_NT, sms);
+        if (qi == mp_batch_plan::Q_FAST2 || qi == mp_batch_plan::Q_FASTP) {
+            const int kind = qi == mp_batch_plan::Q_FAST2 ? mpk::K_P2 : pl->genp_kind;
+            e = kind == mpk::K_P1 ? fast_batch_attr<mpk::K_P1>(pl, qi, sms)
+                : kind == mpk::K_P3 ? fast_batch_attr<mpk::K_P3>(pl, qi, sms)
+                                    : fast_batch_attr<mpk::K_P2>(pl, qi, sms);
         } else if (qi == mp_batch_plan::Q_Z) {
             e = cudaFuncSetAttribute(mpk::sweepz_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(pl->smem[qi]));

@@ -13,9 +13,10 @@
 //                   series in order of decreasing cell count, so the long
 //                   tiles start first and the short ones fill the tail
 //   batch_finalize  keys -> P, I (FP64 polish)
-// One queue per sweep kernel: the two-stream Euclidean sweep (m a multiple
-// of 32), the float-float z-normalised sweep, and the generic FP32 sweep
-// (other m, p-norm) for one exponent kind.
+// One queue per sweep kernel: the two-stream sweep (m a multiple of 32) for
+// p = 2 and for the batch's p-norm exponent when it is 1 or 3, the
+// float-float z-normalised sweep, and the generic FP32 sweep (other m, other
+// p) for p = 2 and for the batch's exponent.
 #pragma once
 
 #include <cstdint>
@@ -142,6 +143,7 @@ __device__ __forceinline__ bool batch_next(const BatchQueue &q, const BatchData 
     return true;
 }
 
+template <int KIND>
 __global__ void __launch_bounds__(V2_NT, 2) sweep2_batch_kernel(const BatchData d, const BatchQueue q) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Sweep2Args sa;
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(V2_NT, 2) sweep2_batch_kernel(const BatchData 
             sa.B = sr->m / V2_QMAX;
         }
         __syncthreads();
-        sweep2_tile(sa, tile.band, tile.rt, smem);
+        sweep2_tile<KIND>(sa, tile.band, tile.rt, smem);
         __syncthreads();
     }
 }

@@ -48,7 +48,6 @@ constexpr int SW_KW = SW_NT * SW_D;  // diagonals per band
 constexpr int SW_QMAX = 8;           // ring blocks per diagonal
 constexpr int SW_W = 2 * SW_D - 1;   // window values per D-row block
 
-enum Kind { K_P2 = 0, K_P1 = 1, K_P3 = 2, K_PG = 3 };
 
 struct SweepArgs {
     const float *hi;  // series (FP32 part), zero beyond n

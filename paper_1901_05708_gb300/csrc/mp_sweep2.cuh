@@ -1,5 +1,6 @@
-// a3-a5, fast path: the Euclidean diagonal sweep (Algorithm 1) for FP32
-// series with m a multiple of 32 (re-anchor interval B = m / 4, Q = 4).
+// a3-a5, fast path: the Euclidean diagonal sweep (Algorithm 1) and the
+// p-norm sweep for p = 1 and 3 (Algorithm 3) for FP32 series with m a
+// multiple of 32 (re-anchor interval B = m / 4, Q = 4).
 //
 // Same decomposition as the generic kernel (bands of KW diagonals, row
 // tiles, D adjacent diagonals per thread), shaped for the FP32 pipes:
@@ -210,8 +211,23 @@ __device__ __forceinline__ float2 v2_sub(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, one rounding
 }
 
+// acc + term(x) for both streams: x^2 (one packed FMA), |x| (two FADDs with an
+// absolute-value operand), |x|^3 = |x| x^2 (a packed multiply and two FMAs).
+template <int KIND>
+__device__ __forceinline__ float2 v2_acc(float2 x, float2 acc) {
+    if constexpr (KIND == K_P1) {
+        return make_float2(acc.x + fabsf(x.x), acc.y + fabsf(x.y));
+    } else if constexpr (KIND == K_P3) {
+        const float2 x2 = __fmul2_rn(x, x);
+        return make_float2(fmaf(fabsf(x.x), x2.x, acc.x), fmaf(fabsf(x.y), x2.y, acc.y));
+    } else {
+        return fma2(x, x, acc);
+    }
+}
+
 // One tile (band, rt) of one problem.  Every thread of the CTA calls it; it
 // synchronises once (after staging) and may return early per thread after that.
+template <int KIND>
 __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band, long long rt,
                                             unsigned char *smem) {
     const int m = a.m, B = a.B, Q = a.Q;
@@ -292,7 +308,7 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
 #pragma unroll
                 for (int d = 0; d < V2_D; ++d) {
                     const float2 e = v2_sub(ti, W[l + d + 1]);
-                    beta[d] = fma2(e, e, beta[d]);
+                    beta[d] = v2_acc<KIND>(e, beta[d]);
                 }
             }
         }
@@ -316,7 +332,7 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
 #pragma unroll
             for (int d = 0; d < V2_D; ++d) {
                 const float2 e = v2_sub(te, WE[ul + d]);
-                E[d] = fma2(e, e, E[d]);
+                E[d] = v2_acc<KIND>(e, E[d]);
                 ring[(anchor_slot * V2_D + d) * V2_NT + tid] = E[d];
                 float2 acc = make_float2(0.f, 0.f);
                 for (int qb = 0; qb < Q; ++qb) acc = add2(acc, ring[(qb * V2_D + d) * V2_NT + tid]);
@@ -331,8 +347,8 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
             for (int d = 0; d < V2_D; ++d) {
                 const float2 e = v2_sub(te, WE[ul + d]);
                 const float2 f = v2_sub(tl, WL[ul + d]);
-                E[d] = fma2(e, e, E[d]);
-                F[d] = fma2(f, f, F[d]);
+                E[d] = v2_acc<KIND>(e, E[d]);
+                F[d] = v2_acc<KIND>(f, F[d]);
                 s[d] = v2_sub(E[d], F[d]);
             }
         }
@@ -473,6 +489,7 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
     }
 }
 
+template <int KIND>
 __global__ void __launch_bounds__(V2_NT, 2) sweep2_kernel(const Sweep2Args a) {
     extern __shared__ __align__(16) unsigned char smem[];
     long long band, rt;
@@ -480,7 +497,7 @@ __global__ void __launch_bounds__(V2_NT, 2) sweep2_kernel(const Sweep2Args a) {
         if (threadIdx.x == 0) atomicOr(&mp_device_error, ERR_BAD_TILE);
         return;
     }
-    sweep2_tile(a, band, rt, smem);
+    sweep2_tile<KIND>(a, band, rt, smem);
 }
 
 }  // namespace mpk

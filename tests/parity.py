@@ -9,8 +9,9 @@ Acceptance (for FP32 sweeps rtol = 1e-5, for FP64 sweeps rtol = 1e-12):
         sqrt(P^2 + 2m Q_ATOL_Z32) - P to the tolerance of its rows;
   (ii)  P[i] equals d(i, I[i]) recomputed by the oracle;
   (iii) I[i] == I_ref[i] wherever the oracle's runner-up (outside the
-        winner's exclusion zone) is more than the tolerance above the best;
-        elsewhere I[i] must still be a valid neighbour within tolerance.
+        winner's exclusion zone, and inside it but not the winner itself) is
+        more than the tolerance above the best; elsewhere I[i] must still be a
+        valid neighbour within tolerance.
 """
 from __future__ import annotations
 
@@ -68,6 +69,18 @@ def check(T, m, excl, dist, p, P, I, rtol, rows=None, P_ref=None, I_ref=None, P2
     # (iii)
     unique = (P2[has] - P_ref[has]) > tol[has]
     mism = unique & (Ig[has] != I_ref[has])
+    if np.any(mism):
+        # P2 skips the winner's own zone; a candidate inside it (a shift of the
+        # same match) can still tie with the winner within tolerance, and then
+        # the index is not unique either
+        hr, hI, hP, ht = rows[has], I_ref[has], P_ref[has], tol[has]
+        for x in np.nonzero(mism)[0]:
+            i, w = int(hr[x]), int(hI[x])
+            js = np.arange(max(0, w - excl), min(N, w + excl + 1))
+            js = js[(js != w) & (np.abs(js - i) > excl)]
+            if js.size and np.min(oracle.pair_dist(T, m, np.full(js.size, i), js, dist, p)) - hP[x] <= ht[x]:
+                unique[x] = False
+        mism = unique & (Ig[has] != I_ref[has])
     assert not np.any(mism), (f"{label}: I differs in {mism.sum()} rows with a unique winner, e.g. row "
                               f"{rows[has][np.argmax(mism)]}: got {Ig[has][np.argmax(mism)]}, "
                               f"want {I_ref[has][np.argmax(mism)]}")

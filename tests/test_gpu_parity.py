@@ -162,28 +162,34 @@ def test_invalid_arguments(mp):
 
 @pytest.mark.parametrize("m", [32, 64, 96])
 def test_integer_fast_path_bit_exact(mp, m):
-    """The two-stream Euclidean kernel (m a multiple of 8, FP32 input) on
-    integer data: P and I equal the oracle exactly, ties included."""
+    """The two-stream kernel (m a multiple of 32, FP32 input) on integer data,
+    for p = 2, 1 and 3: every term and partial sum is an integer below 2^24,
+    so P and I equal the oracle exactly, ties included."""
     rng = np.random.default_rng(900 + m)
     T = rng.integers(-8, 9, 7000).astype(np.float32)
-    for excl in (0, m // 4):
-        Pr, Ir = oracle.brute(T, m, excl, "euclid")
-        P, I = run(mp, T, m, excl, "euclid")
-        np.testing.assert_array_equal(I, Ir)
-        np.testing.assert_array_equal(P, Pr)
+    for dist, p in (("euclid", 2.0), ("pnorm", 1.0), ("pnorm", 3.0)):
+        for excl in (0, m // 4):
+            Pr, Ir = oracle.brute(T, m, excl, dist, p)
+            P, I = run(mp, T, m, excl, dist, p)
+            np.testing.assert_array_equal(I, Ir, err_msg=f"{dist} p={p} excl={excl}")
+            if p == 3.0:  # the final cube root: CUDA's and the C library's pow may differ by an ulp
+                np.testing.assert_allclose(P, Pr, rtol=4e-16, atol=0)
+            else:
+                np.testing.assert_array_equal(P, Pr, err_msg=f"{dist} p={p} excl={excl}")
 
 
-def test_fast_and_generic_kernels_agree(mp, monkeypatch):
-    """Fast and generic FP32 Euclidean kernels against the oracle on a series
-    with many bands and row tiles (n = 40,000, m = 64)."""
+@pytest.mark.parametrize("dist,p", [("euclid", 2.0), ("pnorm", 1.0), ("pnorm", 3.0)])
+def test_fast_and_generic_kernels_agree(mp, monkeypatch, dist, p):
+    """Fast and generic FP32 kernels against the oracle on a series with many
+    bands and row tiles (n = 40,000, m = 64)."""
     s = W.small("motif", 40_000, 64, 81, dtype=np.float32)
     rows = np.random.default_rng(1).choice(s.N, 400, replace=False)
-    ref = oracle.brute_rows(s.T, s.m, s.excl, rows, "euclid")
-    P1, I1 = run(mp, s.T, s.m, s.excl, "euclid")
+    ref = oracle.brute_rows(s.T, s.m, s.excl, rows, dist, p)
+    P1, I1 = run(mp, s.T, s.m, s.excl, dist, p)
     monkeypatch.setenv("MP_FORCE_GENERIC", "1")
-    P2, I2 = run(mp, s.T, s.m, s.excl, "euclid")
+    P2, I2 = run(mp, s.T, s.m, s.excl, dist, p)
     for P, I, lab in ((P1, I1, "fast"), (P2, I2, "generic")):
-        parity.check(s.T, s.m, s.excl, "euclid", 2.0, P, I, RTOL32, rows=rows,
+        parity.check(s.T, s.m, s.excl, dist, p, P, I, RTOL32, rows=rows,
                      P_ref=ref[0], I_ref=ref[1], P2=ref[2], label=lab)
     agree = np.mean(I1 == I2)
     assert agree > 0.999, agree
