@@ -6,9 +6,11 @@
 // (Lemma 3's sums rewritten around the window means; df, dg, inv = 1/sqrt(S)
 // come from the FP64 statistics kernel) and scores each cell with
 //   q = 1 - rho = 1 - cov inv_i inv_j          (DZ^2 = 2 m q, Lemma 3).
-// FP32 cannot hold cov to the 1e-9 relative that q ~ 0.01 needs over tens of
-// thousands of steps, so cov is a float-float pair (hi, lo) updated with an
-// error-free Fast2Sum: 9 packed f32x2 operations per cell pair.
+// FP32 cannot hold cov to the 1e-9 relative that q ~ 0.01 needs over
+// thousands of steps, so cov is a float-float pair (hi, lo): each step adds
+// its increment to the low word (one packed operation) and an error-free
+// Fast2Sum folds the low word into the high word every second row: 7.5
+// packed f32x2 operations per cell pair.
 //
 // Tiles are tall (a band of KW diagonals by up to S rows, split into two row
 // streams packed in f32x2 as in the Euclidean fast path), so the anchor of
@@ -228,14 +230,23 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
             cb[j] = NONE;
         };
         // one covariance step into chunk row ul, partner window offset o
+        // The increments go into the low word only; renorm() folds it into the
+        // high word with an error-free Fast2Sum after every second row, so the
+        // low word never holds more than two increments and its rounding stays
+        // at the size of the increments' own rounding.
         auto step = [&](int ul, const float2 *WF, const float2 *WG, int o) {
             const float2 fi = IF[ul], gi = IG[ul];
 #pragma unroll
             for (int d = 0; d < Z_D; ++d) {
                 const float2 inc = fma2(fi, WG[o + d], z_mul(WF[o + d], gi));  // df_i dg_j + df_j dg_i
-                const float2 t = v2_sub(ch[d], inc);                               // Fast2Sum(ch, -inc)
-                const float2 z = v2_sub(t, ch[d]);
-                cl[d] = v2_sub(cl[d], add2(inc, z));
+                cl[d] = v2_sub(cl[d], inc);
+            }
+        };
+        auto renorm = [&]() {
+#pragma unroll
+            for (int d = 0; d < Z_D; ++d) {
+                const float2 t = add2(ch[d], cl[d]);  // Fast2Sum(ch, cl)
+                cl[d] = v2_sub(cl[d], v2_sub(t, ch[d]));
                 ch[d] = t;
             }
         };
@@ -278,6 +289,7 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                     step(ulb + ul1, WF, WG, ul1);
 #pragma unroll
                     for (int d = 0; d < Z_D; ++d) q[d] = score(II[ulb + ul1], WI[ul1 + d], d);
+                    renorm();
                     v2_tag8(t1a, q, false, tag_mask);
                     v2_tag8(t1b, q, true, tag_mask);
                     const float r0a = v2_min8(t0a), r0b = v2_min8(t0b), r1a = v2_min8(t1a), r1b = v2_min8(t1b);
@@ -332,6 +344,7 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                         WGr[d] = JG[px];
                     }
                     step(ul, WFr, WGr, 0);
+                    renorm();
                     masked_row(u, ul, ui % Z_D);
                     ulast = u;
                 }
