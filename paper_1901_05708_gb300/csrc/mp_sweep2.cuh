@@ -81,6 +81,18 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
     return r;
 }
 
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// The block filter pays off where few scores come near the thresholds
+// (random walks, the Euclidean workloads); on series with many near matches
+// (periodic signals) its failed passes cost more than they save.  It is on
+// for p = 2 only.
+#define V2_FILTER(KIND) ((KIND) == K_P2)
+
 // ---- tile enumeration ---------------------------------------------------------------
 // Band b (diagonals k_first + b KW ...) has L_b = L - b KW rows and
 // ceil(L_b / R) row tiles.  The first tile of band b is
@@ -382,13 +394,35 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
         cb[j] = NONE;
     };
 
+    // Offer the partial minima of the columns still open after row ul
+    // (slot sl holds column ul + ((sl - ul) mod D)) and close them: every
+    // contribution is a genuine cell value, so emitting it early is exact.
+    auto flush_open = [&](int ul) {
+#pragma unroll
+        for (int sl = 0; sl < V2_D; ++sl) {
+            const int delta = ((sl - ul) % V2_D + V2_D) % V2_D;
+            if (delta != 0) {
+                const int uc = ul + delta;
+                if (ca[sl] != NONE && ca[sl] <= thr_c[col_idx(uc, 0)])
+                    v2_emit(a.keys, thr_c, col_idx(uc, 0), col_tgt(uc, 0), ca[sl], kt, 0);
+                if (cb[sl] != NONE && cb[sl] <= thr_c[col_idx(uc, 1)])
+                    v2_emit(a.keys, thr_c, col_idx(uc, 1), col_tgt(uc, 1), cb[sl], kt, 0);
+            }
+            ca[sl] = NONE;
+            cb[sl] = NONE;
+        }
+    };
+
     // ---- row 0: the anchors themselves
 #pragma unroll
     for (int d = 0; d < V2_D; ++d) { ca[d] = NONE; cb[d] = NONE; }
     masked_row(0, 0);
+    if (V2_FILTER(KIND)) flush_open(0);
 
     // ---- fast region: 8-row blocks (ub, ub + 8] with every cell valid --------------
     int ub = 0;
+    int skip = 0, backoff = 1;  // blocks to run tracked without a filter pass; next skip length
+    constexpr bool kFilter = V2_FILTER(KIND);
     for (; ub + V2_D < ufast; ub += V2_D) {
         float2 WL[2 * V2_D], WE[2 * V2_D];
         {
@@ -404,57 +438,119 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
             }
         }
         const bool anc = ub + V2_D == next_anchor;  // B % 8 == 0: anchors fall on a block's last row
-        // per-block bases, so that every access below uses a constant offset
-        const float *tra = thr_r + ub, *trb = thr_r + V2_H + ub;
-        float *tca = thr_c + v2_cpos(jb + ub), *tcb = thr_c + v2_cpos(jb + Ht + ub);  // jb + ub, Ht: multiples of 8
-        const float2 *itl = IT + ub, *ite = IT + ub + m;
+        // ---- filter pass (p = 2): the recurrence and one running minimum
+        // over the block's 128 scores.  In the steady state no score of the
+        // block reaches the loosest threshold of the rows and columns it feeds,
+        // and the block costs the recurrence plus half an instruction per
+        // cell.  The decision is taken for the warp's active lanes together
+        // (one lane that needs the tracked pass costs the warp that pass
+        // anyway); after a failed filter the next blocks go straight to the
+        // tracked pass, for a number of blocks that doubles while the filter
+        // keeps failing.
+        bool track = true;
+        if (kFilter && skip > 0) {
+            --skip;
+        } else if (kFilter) {
+            float2 E0[V2_D], F0[V2_D];
 #pragma unroll
-        for (int pr = 0; pr < V2_D / 2; ++pr) {
-            const int ul0 = 2 * pr + 1, ul1 = ul0 + 1;  // rows u0 = ub + ul0, u1 = ub + ul1
-            const int cp0 = ul0 + (ul0 >> 3), cp1 = ul1 + (ul1 >> 3);  // padded column offsets
-            float t0a[V2_D], t0b[V2_D], t1a[V2_D], t1b[V2_D];
-            step(false, itl[ul0], ite[ul0], WL, WE, ul0);
-            v2_tag8(t0a, s, false, tag_mask);
-            v2_tag8(t0b, s, true, tag_mask);
-            step(pr == V2_D / 2 - 1 && anc, itl[ul1], ite[ul1], WL, WE, ul1);
-            v2_tag8(t1a, s, false, tag_mask);
-            v2_tag8(t1b, s, true, tag_mask);
-            const float r0a = v2_min8(t0a), r0b = v2_min8(t0b), r1a = v2_min8(t1a), r1b = v2_min8(t1b);
-            // columns: slot j0 = u0 % D completes column u0, slot j1 completes column u1
-            const int j0 = ul0 % V2_D, j1 = ul1 % V2_D;
+            for (int d = 0; d < V2_D; ++d) { E0[d] = E[d]; F0[d] = F[d]; }
+            const int slot0 = anchor_slot, next0 = next_anchor;
+            float bmin = NONE;
+            {
+                const float2 *itl0 = IT + ub, *ite0 = IT + ub + m;
 #pragma unroll
-            for (int jj = 0; jj < V2_D; ++jj) {
-                const int sl = (j0 + jj) % V2_D;
-                if (jj == 0) {
-                    ca[sl] = fminf(ca[sl], t0a[0]);
-                    cb[sl] = fminf(cb[sl], t0b[0]);
-                } else if (jj < V2_D - 1) {
-                    ca[sl] = min3f(ca[sl], t0a[jj], t1a[jj - 1]);
-                    cb[sl] = min3f(cb[sl], t0b[jj], t1b[jj - 1]);
-                } else {
-                    ca[sl] = fminf(t0a[jj], t1a[jj - 1]);
-                    cb[sl] = fminf(t0b[jj], t1b[jj - 1]);
+                for (int ul = 1; ul <= V2_D; ++ul) {
+                    step(ul == V2_D && anc, itl0[ul], ite0[ul], WL, WE, ul);
+#pragma unroll
+                    for (int d = 0; d < V2_D; ++d) bmin = min3f(bmin, s[d].x, s[d].y);
                 }
             }
-            // one test for the 8 candidates of this pair of rows; the rare
-            // pass re-tests each and emits it
-            const int any = v2_any_le(r0a, tra[ul0], r0b, trb[ul0], r1a, tra[ul1], r1b, trb[ul1], ca[j0],
-                                      tca[cp0], cb[j0], tcb[cp0], ca[j1], tca[cp1], cb[j1], tcb[cp1]);
-            if (__builtin_expect(any != 0, 0)) {
-                const int u0 = ub + ul0, u1 = ub + ul1;
-                if (r0a <= tra[ul0]) v2_emit(a.keys, thr_r, u0, row_tgt(u0, 0), r0a, kt, 1);
-                if (r0b <= trb[ul0]) v2_emit(a.keys, thr_r, V2_H + u0, row_tgt(u0, 1), r0b, kt, 1);
-                if (r1a <= tra[ul1]) v2_emit(a.keys, thr_r, u1, row_tgt(u1, 0), r1a, kt, 1);
-                if (r1b <= trb[ul1]) v2_emit(a.keys, thr_r, V2_H + u1, row_tgt(u1, 1), r1b, kt, 1);
-                if (ca[j0] <= tca[cp0]) v2_emit(a.keys, thr_c, col_idx(u0, 0), col_tgt(u0, 0), ca[j0], kt, 0);
-                if (cb[j0] <= tcb[cp0]) v2_emit(a.keys, thr_c, col_idx(u0, 1), col_tgt(u0, 1), cb[j0], kt, 0);
-                if (ca[j1] <= tca[cp1]) v2_emit(a.keys, thr_c, col_idx(u1, 0), col_tgt(u1, 0), ca[j1], kt, 0);
-                if (cb[j1] <= tcb[cp1]) v2_emit(a.keys, thr_c, col_idx(u1, 1), col_tgt(u1, 1), cb[j1], kt, 0);
+            // thresholds of the 2 x 8 rows and 2 x 15 columns the block feeds
+            const float *fra = thr_r + ub, *frb = thr_r + V2_H + ub;
+            const float *fca = thr_c + v2_cpos(jb + ub), *fcb = thr_c + v2_cpos(jb + Ht + ub);
+            float tmax = max3f(fra[1], fra[2], fra[3]);
+            tmax = max3f(tmax, fra[4], fra[5]);
+            tmax = max3f(tmax, fra[6], fra[7]);
+            tmax = max3f(tmax, fra[8], frb[1]);
+            tmax = max3f(tmax, frb[2], frb[3]);
+            tmax = max3f(tmax, frb[4], frb[5]);
+            tmax = max3f(tmax, frb[6], frb[7]);
+            tmax = max3f(tmax, frb[8], fca[1]);
+#pragma unroll
+            for (int x = 2; x < 2 * V2_D; x += 2) tmax = max3f(tmax, fca[x + (x >> 3)], fca[x + 1 + ((x + 1) >> 3)]);
+#pragma unroll
+            for (int x = 1; x < 2 * V2_D - 1; x += 2) tmax = max3f(tmax, fcb[x + (x >> 3)], fcb[x + 1 + ((x + 1) >> 3)]);
+            tmax = fmaxf(tmax, fcb[2 * V2_D - 1 + ((2 * V2_D - 1) >> 3)]);
+            // a tagged score is at least the score with its tag bits cleared
+            track = __any_sync(__activemask(), __int_as_float(__float_as_int(bmin) & tag_mask) <= tmax);
+            if (__builtin_expect(track, 0)) {  // replay the block from the saved state, tracked
+#pragma unroll
+                for (int d = 0; d < V2_D; ++d) { E[d] = E0[d]; F[d] = F0[d]; }
+                anchor_slot = slot0;
+                next_anchor = next0;
+                skip = backoff;
+                backoff = backoff < 32 ? 2 * backoff : 32;
+            } else {
+                backoff = 1;
             }
-            ca[j0] = t1a[V2_D - 1];
-            cb[j0] = t1b[V2_D - 1];
-            ca[j1] = NONE;
-            cb[j1] = NONE;
+        }
+        if (track) {
+            // ---- tracked pass of the block
+            // per-block bases, so that every access below uses a constant offset
+            const float *tra = thr_r + ub, *trb = thr_r + V2_H + ub;
+            float *tca = thr_c + v2_cpos(jb + ub), *tcb = thr_c + v2_cpos(jb + Ht + ub);  // jb + ub, Ht: multiples of 8
+            const float2 *itl = IT + ub, *ite = IT + ub + m;
+#pragma unroll
+            for (int pr = 0; pr < V2_D / 2; ++pr) {
+                const int ul0 = 2 * pr + 1, ul1 = ul0 + 1;  // rows u0 = ub + ul0, u1 = ub + ul1
+                const int cp0 = ul0 + (ul0 >> 3), cp1 = ul1 + (ul1 >> 3);  // padded column offsets
+                float t0a[V2_D], t0b[V2_D], t1a[V2_D], t1b[V2_D];
+                step(false, itl[ul0], ite[ul0], WL, WE, ul0);
+                v2_tag8(t0a, s, false, tag_mask);
+                v2_tag8(t0b, s, true, tag_mask);
+                step(pr == V2_D / 2 - 1 && anc, itl[ul1], ite[ul1], WL, WE, ul1);
+                v2_tag8(t1a, s, false, tag_mask);
+                v2_tag8(t1b, s, true, tag_mask);
+                const float r0a = v2_min8(t0a), r0b = v2_min8(t0b), r1a = v2_min8(t1a), r1b = v2_min8(t1b);
+                // columns: slot j0 = u0 % D completes column u0, slot j1 completes column u1
+                const int j0 = ul0 % V2_D, j1 = ul1 % V2_D;
+#pragma unroll
+                for (int jj = 0; jj < V2_D; ++jj) {
+                    const int sl = (j0 + jj) % V2_D;
+                    if (jj == 0) {
+                        ca[sl] = fminf(ca[sl], t0a[0]);
+                        cb[sl] = fminf(cb[sl], t0b[0]);
+                    } else if (jj < V2_D - 1) {
+                        ca[sl] = min3f(ca[sl], t0a[jj], t1a[jj - 1]);
+                        cb[sl] = min3f(cb[sl], t0b[jj], t1b[jj - 1]);
+                    } else {
+                        ca[sl] = fminf(t0a[jj], t1a[jj - 1]);
+                        cb[sl] = fminf(t0b[jj], t1b[jj - 1]);
+                    }
+                }
+                // one test for the 8 candidates of this pair of rows; the rare
+                // pass re-tests each and emits it
+                const int any = v2_any_le(r0a, tra[ul0], r0b, trb[ul0], r1a, tra[ul1], r1b, trb[ul1], ca[j0],
+                                          tca[cp0], cb[j0], tcb[cp0], ca[j1], tca[cp1], cb[j1], tcb[cp1]);
+                if (__builtin_expect(any != 0, 0)) {
+                    const int u0 = ub + ul0, u1 = ub + ul1;
+                    if (r0a <= tra[ul0]) v2_emit(a.keys, thr_r, u0, row_tgt(u0, 0), r0a, kt, 1);
+                    if (r0b <= trb[ul0]) v2_emit(a.keys, thr_r, V2_H + u0, row_tgt(u0, 1), r0b, kt, 1);
+                    if (r1a <= tra[ul1]) v2_emit(a.keys, thr_r, u1, row_tgt(u1, 0), r1a, kt, 1);
+                    if (r1b <= trb[ul1]) v2_emit(a.keys, thr_r, V2_H + u1, row_tgt(u1, 1), r1b, kt, 1);
+                    if (ca[j0] <= tca[cp0]) v2_emit(a.keys, thr_c, col_idx(u0, 0), col_tgt(u0, 0), ca[j0], kt, 0);
+                    if (cb[j0] <= tcb[cp0]) v2_emit(a.keys, thr_c, col_idx(u0, 1), col_tgt(u0, 1), cb[j0], kt, 0);
+                    if (ca[j1] <= tca[cp1]) v2_emit(a.keys, thr_c, col_idx(u1, 0), col_tgt(u1, 0), ca[j1], kt, 0);
+                    if (cb[j1] <= tcb[cp1]) v2_emit(a.keys, thr_c, col_idx(u1, 1), col_tgt(u1, 1), cb[j1], kt, 0);
+                }
+                ca[j0] = t1a[V2_D - 1];
+                cb[j0] = t1b[V2_D - 1];
+                ca[j1] = NONE;
+                cb[j1] = NONE;
+            }
+            // the slots are empty when a block starts: a filtered block needs no
+            // column state from its predecessor
+            if (kFilter) flush_open(ub + V2_D);
         }
     }
 
