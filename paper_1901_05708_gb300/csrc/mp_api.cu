@@ -229,18 +229,23 @@ bool fast_path_ok(const Problem &pb) {
            mpk::sweep2_smem_bytes(pb.m, mpk::V2_QMAX) <= mpk::V2_SMEM_MAX && !getenv_generic();
 }
 
-template <int KIND>
+template <int KIND, bool FILTER>
 mp_status launch_sweep2_t(const mpk::Sweep2Args &a, size_t smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(mpk::sweep2_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(mpk::sweep2_kernel<KIND, FILTER>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(sweep2)");
     {
         SweepEvents ev(st);
-        mpk::sweep2_kernel<KIND><<<static_cast<unsigned>(a.tiles), mpk::V2_NT, smem, st>>>(a);
+        mpk::sweep2_kernel<KIND, FILTER><<<static_cast<unsigned>(a.tiles), mpk::V2_NT, smem, st>>>(a);
     }
     counted();
     return MP_OK;
 }
+
+// The Euclidean sweep's block filter pays off once thresholds are tight for most
+// of the sweep, i.e. on long series (each row meets many tiles); on short
+// series and on the p-norm kernels (periodic data) it fails too often.
+constexpr long long FILTER_MIN_N = 200000;
 
 mp_status run_sweep2(const Problem &pb, const Layout &L, char *ws, cudaStream_t st) {
     mpk::Sweep2Args a{};
@@ -260,9 +265,11 @@ mp_status run_sweep2(const Problem &pb, const Layout &L, char *ws, cudaStream_t 
     if (a.tiles <= 0) return MP_OK;
     const size_t smem = mpk::sweep2_smem_bytes(a.m, a.Q);
     switch (kind_of(pb.dist, pb.p)) {
-        case mpk::K_P1: return launch_sweep2_t<mpk::K_P1>(a, smem, st);
-        case mpk::K_P3: return launch_sweep2_t<mpk::K_P3>(a, smem, st);
-        default: return launch_sweep2_t<mpk::K_P2>(a, smem, st);
+        case mpk::K_P1: return launch_sweep2_t<mpk::K_P1, false>(a, smem, st);
+        case mpk::K_P3: return launch_sweep2_t<mpk::K_P3, false>(a, smem, st);
+        default:
+            return pb.N >= FILTER_MIN_N ? launch_sweep2_t<mpk::K_P2, true>(a, smem, st)
+                                        : launch_sweep2_t<mpk::K_P2, false>(a, smem, st);
     }
 }
 

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(V2_NT, 2) sweep2_batch_kernel(const BatchData 
             sa.B = sr->m / V2_QMAX;
         }
         __syncthreads();
-        sweep2_tile<KIND>(sa, tile.band, tile.rt, smem);
+        sweep2_tile<KIND, false>(sa, tile.band, tile.rt, smem);
         __syncthreads();
     }
 }

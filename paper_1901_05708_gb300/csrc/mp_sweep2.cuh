@@ -87,11 +87,6 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
     return r;
 }
 
-// The block filter pays off where few scores come near the thresholds
-// (random walks, the Euclidean workloads); on series with many near matches
-// (periodic signals) its failed passes cost more than they save.  It is on
-// for p = 2 only.
-#define V2_FILTER(KIND) ((KIND) == K_P2)
 
 // ---- tile enumeration ---------------------------------------------------------------
 // Band b (diagonals k_first + b KW ...) has L_b = L - b KW rows and
@@ -150,7 +145,7 @@ inline size_t sweep2_smem_bytes(int m, int Q) {
     const size_t nj = v2_jpos(V2_KW + V2_H + m + 16) + 2;
     const size_t ni = V2_H + m + 16;
     const size_t nc = v2_cpos(V2_KW + 2 * V2_H + 16);
-    return (nj + ni) * sizeof(float2) + (2 * V2_H + nc) * sizeof(float) +
+    return (nj + ni) * sizeof(float2) + (2 * V2_H + 4 + nc) * sizeof(float) +
            static_cast<size_t>(Q) * V2_D * V2_NT * sizeof(float2);
 }
 
@@ -239,7 +234,7 @@ __device__ __forceinline__ float2 v2_acc(float2 x, float2 acc) {
 
 // One tile (band, rt) of one problem.  Every thread of the CTA calls it; it
 // synchronises once (after staging) and may return early per thread after that.
-template <int KIND>
+template <int KIND, bool FILTER>
 __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band, long long rt,
                                             unsigned char *smem) {
     const int m = a.m, B = a.B, Q = a.Q;
@@ -260,8 +255,10 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
     const int njs = v2_jpos(V2_KW + V2_H + m + 16) + 2;
     float2 *JT = reinterpret_cast<float2 *>(smem);
     float2 *IT = JT + njs;
-    float *thr_r = reinterpret_cast<float *>(IT + (V2_H + m + 16));
-    float *thr_c = thr_r + 2 * V2_H;
+    // thr_r is offset by 3 floats from a 16-byte boundary, so that the
+    // thresholds of rows 8g+1 .. 8g+4 and 8g+5 .. 8g+8 are 16-byte loads
+    float *thr_r = reinterpret_cast<float *>(IT + (V2_H + m + 16)) + 3;
+    float *thr_c = thr_r + 2 * V2_H + 1;
     float2 *ring = reinterpret_cast<float2 *>(thr_c + v2_cpos(V2_KW + 2 * V2_H + 16));
 
     const long long y0 = r0 + k0 - 1;
@@ -417,12 +414,14 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
 #pragma unroll
     for (int d = 0; d < V2_D; ++d) { ca[d] = NONE; cb[d] = NONE; }
     masked_row(0, 0);
-    if (V2_FILTER(KIND)) flush_open(0);
+    if (FILTER) flush_open(0);  // with the filter, column slots never cross a block boundary
 
     // ---- fast region: 8-row blocks (ub, ub + 8] with every cell valid --------------
     int ub = 0;
     int skip = 0, backoff = 1;  // blocks to run tracked without a filter pass; next skip length
-    constexpr bool kFilter = V2_FILTER(KIND);
+    bool group_valid = false;   // gca, gcb hold the column maxima for this block's columns 1..8
+    float gca = NONE, gcb = NONE;
+    constexpr bool kFilter = FILTER;
     for (; ub + V2_D < ufast; ub += V2_D) {
         float2 WL[2 * V2_D], WE[2 * V2_D];
         {
@@ -450,39 +449,67 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
         bool track = true;
         if (kFilter && skip > 0) {
             --skip;
+            group_valid = false;
         } else if (kFilter) {
             float2 E0[V2_D], F0[V2_D];
 #pragma unroll
             for (int d = 0; d < V2_D; ++d) { E0[d] = E[d]; F0[d] = F[d]; }
             const int slot0 = anchor_slot, next0 = next_anchor;
-            float bmin = NONE;
+            float bma = NONE, bmb = NONE;
             {
                 const float2 *itl0 = IT + ub, *ite0 = IT + ub + m;
 #pragma unroll
                 for (int ul = 1; ul <= V2_D; ++ul) {
                     step(ul == V2_D && anc, itl0[ul], ite0[ul], WL, WE, ul);
 #pragma unroll
-                    for (int d = 0; d < V2_D; ++d) bmin = min3f(bmin, s[d].x, s[d].y);
+                    for (int d = 0; d < V2_D; d += 2) {
+                        bma = min3f(bma, s[d].x, s[d + 1].x);
+                        bmb = min3f(bmb, s[d].y, s[d + 1].y);
+                    }
                 }
             }
-            // thresholds of the 2 x 8 rows and 2 x 15 columns the block feeds
-            const float *fra = thr_r + ub, *frb = thr_r + V2_H + ub;
+            // loosest thresholds of the 8 rows and 15 columns each stream's
+            // scores feed; the maximum over columns 8g+1 .. 8g+8 is the one
+            // read with the previous block (thresholds only decrease, so an
+            // older read is looser)
+            const float4 ra0 = *reinterpret_cast<const float4 *>(thr_r + ub + 1);
+            const float4 ra1 = *reinterpret_cast<const float4 *>(thr_r + ub + 5);
+            const float4 rb0 = *reinterpret_cast<const float4 *>(thr_r + V2_H + ub + 1);
+            const float4 rb1 = *reinterpret_cast<const float4 *>(thr_r + V2_H + ub + 5);
             const float *fca = thr_c + v2_cpos(jb + ub), *fcb = thr_c + v2_cpos(jb + Ht + ub);
-            float tmax = max3f(fra[1], fra[2], fra[3]);
-            tmax = max3f(tmax, fra[4], fra[5]);
-            tmax = max3f(tmax, fra[6], fra[7]);
-            tmax = max3f(tmax, fra[8], frb[1]);
-            tmax = max3f(tmax, frb[2], frb[3]);
-            tmax = max3f(tmax, frb[4], frb[5]);
-            tmax = max3f(tmax, frb[6], frb[7]);
-            tmax = max3f(tmax, frb[8], fca[1]);
-#pragma unroll
-            for (int x = 2; x < 2 * V2_D; x += 2) tmax = max3f(tmax, fca[x + (x >> 3)], fca[x + 1 + ((x + 1) >> 3)]);
-#pragma unroll
-            for (int x = 1; x < 2 * V2_D - 1; x += 2) tmax = max3f(tmax, fcb[x + (x >> 3)], fcb[x + 1 + ((x + 1) >> 3)]);
-            tmax = fmaxf(tmax, fcb[2 * V2_D - 1 + ((2 * V2_D - 1) >> 3)]);
+            if (!group_valid) {  // columns 1..8 of the block sit at padded offsets 1..7, 9
+                gca = max3f(fca[1], fca[2], fca[3]);
+                gcb = max3f(fcb[1], fcb[2], fcb[3]);
+                gca = max3f(gca, fca[4], fca[5]);
+                gcb = max3f(gcb, fcb[4], fcb[5]);
+                gca = max3f(gca, fca[6], fca[7]);
+                gcb = max3f(gcb, fcb[6], fcb[7]);
+                gca = fmaxf(gca, fca[9]);
+                gcb = fmaxf(gcb, fcb[9]);
+            }
+            // columns 9..16 at padded offsets 10..16, 18 (16 is the next block's first)
+            float uga = max3f(fca[10], fca[11], fca[12]), ugb = max3f(fcb[10], fcb[11], fcb[12]);
+            uga = max3f(uga, fca[13], fca[14]);
+            ugb = max3f(ugb, fcb[13], fcb[14]);
+            uga = max3f(uga, fca[15], fca[16]);
+            ugb = max3f(ugb, fcb[15], fcb[16]);
+            uga = fmaxf(uga, fca[18]);
+            ugb = fmaxf(ugb, fcb[18]);
+            float tma = max3f(ra0.x, ra0.y, ra0.z), tmb = max3f(rb0.x, rb0.y, rb0.z);
+            tma = max3f(tma, ra0.w, ra1.x);
+            tmb = max3f(tmb, rb0.w, rb1.x);
+            tma = max3f(tma, ra1.y, ra1.z);
+            tmb = max3f(tmb, rb1.y, rb1.z);
+            tma = max3f(tma, ra1.w, gca);
+            tmb = max3f(tmb, rb1.w, gcb);
+            tma = fmaxf(tma, uga);
+            tmb = fmaxf(tmb, ugb);
+            gca = uga;
+            gcb = ugb;
+            group_valid = true;
             // a tagged score is at least the score with its tag bits cleared
-            track = __any_sync(__activemask(), __int_as_float(__float_as_int(bmin) & tag_mask) <= tmax);
+            track = __any_sync(__activemask(), __int_as_float(__float_as_int(bma) & tag_mask) <= tma ||
+                                                   __int_as_float(__float_as_int(bmb) & tag_mask) <= tmb);
             if (__builtin_expect(track, 0)) {  // replay the block from the saved state, tracked
 #pragma unroll
                 for (int d = 0; d < V2_D; ++d) { E[d] = E0[d]; F[d] = F0[d]; }
@@ -548,8 +575,6 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
                 ca[j1] = NONE;
                 cb[j1] = NONE;
             }
-            // the slots are empty when a block starts: a filtered block needs no
-            // column state from its predecessor
             if (kFilter) flush_open(ub + V2_D);
         }
     }
@@ -585,7 +610,7 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
     }
 }
 
-template <int KIND>
+template <int KIND, bool FILTER>
 __global__ void __launch_bounds__(V2_NT, 2) sweep2_kernel(const Sweep2Args a) {
     extern __shared__ __align__(16) unsigned char smem[];
     long long band, rt;
@@ -593,7 +618,7 @@ __global__ void __launch_bounds__(V2_NT, 2) sweep2_kernel(const Sweep2Args a) {
         if (threadIdx.x == 0) atomicOr(&mp_device_error, ERR_BAD_TILE);
         return;
     }
-    sweep2_tile<KIND>(a, band, rt, smem);
+    sweep2_tile<KIND, FILTER>(a, band, rt, smem);
 }
 
 }  // namespace mpk

@@ -178,6 +178,33 @@ def test_integer_fast_path_bit_exact(mp, m):
                 np.testing.assert_array_equal(P, Pr, err_msg=f"{dist} p={p} excl={excl}")
 
 
+@pytest.mark.parametrize("excl", [0, 8])
+def test_integer_long_series_bit_exact(mp, excl):
+    """Long series (N >= 200,000) take the Euclidean kernel with the per-block
+    filter; on integer data every FP32 value is exact, so P and I must equal
+    the FP64 oracle's (Algorithm 1) everywhere, ties included."""
+    rng = np.random.default_rng(77 + excl)
+    T = rng.integers(-8, 9, 210_000).astype(np.float32)
+    m = 32
+    Pr, Ir = oracle.aamp(T.astype(np.float64), m, excl)
+    P, I = run(mp, T, m, excl, "euclid")
+    np.testing.assert_array_equal(I, Ir)
+    np.testing.assert_array_equal(P, Pr)
+
+
+def test_long_walk_filter_kernel(mp):
+    """A 300,000-point random walk with a planted motif (filter kernel): sampled
+    rows by brute force, the motif rows included."""
+    s = W.small("motif", 300_000, 64, 83, dtype=np.float32)
+    rows = np.unique(np.concatenate([np.random.default_rng(2).choice(s.N, 300, replace=False), [0, s.N - 1]]))
+    ref = oracle.brute_rows(s.T, s.m, s.excl, rows, "euclid")
+    P, I = run(mp, s.T, s.m, s.excl, "euclid")
+    parity.check(s.T, s.m, s.excl, "euclid", 2.0, P, I, RTOL32, rows=rows, P_ref=ref[0], I_ref=ref[1], P2=ref[2],
+                 label="long walk")
+    x = np.arange(s.N)
+    assert np.all(I >= 0) and np.all(np.abs(I - x) > s.excl)
+
+
 @pytest.mark.parametrize("dist,p", [("euclid", 2.0), ("pnorm", 1.0), ("pnorm", 3.0)])
 def test_fast_and_generic_kernels_agree(mp, monkeypatch, dist, p):
     """Fast and generic FP32 kernels against the oracle on a series with many
