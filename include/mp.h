@@ -239,6 +239,47 @@ int64_t mp_batch_tiles(const mp_batch_plan *plan);
  * the plan's last run has completed. */
 mp_status mp_batch_plan_destroy(mp_batch_plan *plan);
 
+/* ---- Streaming append: keep a profile current as samples arrive ----------
+ *
+ * Sec. 1 of the paper notes that the incremental formulation also serves to
+ * maintain the profile of a growing series, without spelling out the method.
+ * Here it is the diagonal recurrence (Lemma 1 / 2 / 3) run on the new last
+ * row: appending one sample creates window j = N; each diagonal k = j - i
+ * moves from its last cell (i - 1, j - 1) to (i, j) in O(1) (the new diagonal
+ * k = j from the definition) and the cell is offered to rows i and j, so an
+ * append costs O(N) and leaves P and I equal to the profile of the longer
+ * series (the same distances, exclusion zone and tie rule as mp_aamp).
+ * The per-diagonal state is FP64 and is recomputed from the definitions every
+ * opt->reanchor appends (0: every 256); a row's new best is rescored from
+ * the definition, so P carries no drift.  The object owns its device memory
+ * (sized for n_max samples); appends are asynchronous on `stream`.
+ */
+typedef struct mp_stream mp_stream;
+
+/* Profile of T (device, n samples of dtype) with distance `dist` (p for
+ * MP_DIST_PNORM), room for n_max samples in all.  The initial profile runs the
+ * one-shot path with opt (precision; polish is forced on) on a workspace
+ * allocated and freed on `stream` for this call.  Errors: as mp_aamp, plus
+ * MP_ERR_INVALID_ARG for n_max < n or a bad dist, MP_ERR_UNSUPPORTED for
+ * opt->k_begin / k_end != 0 or n_max - m + 1 >= 2^31, MP_ERR_CUDA when the
+ * device memory cannot be allocated (nothing is leaked). */
+mp_status mp_stream_create(int dist, const void *T, int dtype, int64_t n, int64_t n_max,
+                           int32_t m, int64_t excl, double p, const mp_options *opt,
+                           mp_stream **out, void *stream);
+
+/* Append `count` samples (device pointer x of dtype).  Fails with
+ * MP_ERR_UNSUPPORTED, appending nothing, if the capacity would be exceeded. */
+mp_status mp_stream_append(mp_stream *s, const void *x, int dtype, int64_t count, void *stream);
+
+/* Copy the current profile (mp_stream_windows(s) entries) into device P, I. */
+mp_status mp_stream_read(const mp_stream *s, double *P, int64_t *I, void *stream);
+
+/* Current number of windows N = n - m + 1, or -1 for a NULL stream. */
+int64_t mp_stream_windows(const mp_stream *s);
+
+/* Free the stream's device memory (after its last append has completed). */
+mp_status mp_stream_destroy(mp_stream *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,7 @@
 #include "mp_sweep_z2.cuh"
 #include "mp_launch.cuh"
 #include "mp_batch.cuh"
+#include "mp_stream.cuh"
 
 namespace {
 
@@ -996,6 +997,221 @@ int64_t mp_batch_tiles(const mp_batch_plan *plan) {
 
 mp_status mp_batch_plan_destroy(mp_batch_plan *plan) {
     batch_free(plan);
+    return MP_OK;
+}
+
+}  // extern "C"
+
+// ---- streaming append -----------------------------------------------------------------
+struct mp_stream {
+    int device = -1;
+    int dist = MP_DIST_EUCLID;
+    int m = 0;
+    long long excl = 0;
+    double p = 2.0;
+    long long n = 0, N = 0, n_max = 0, N_max = 0;
+    int reanchor = 4096;
+    long long since_anchor = 0;
+    double *x64 = nullptr, *state = nullptr, *R = nullptr, *P = nullptr, *mu = nullptr, *S = nullptr;
+    long long *I = nullptr;
+    unsigned char *flat = nullptr;
+    double *part_r = nullptr;
+    long long *part_k = nullptr;
+    unsigned *counter = nullptr;
+};
+
+namespace {
+
+void stream_free(mp_stream *s) {
+    if (!s) return;
+    void *ptrs[] = {s->x64, s->state, s->R, s->P, s->mu, s->S, s->I, s->flat, s->part_r, s->part_k, s->counter};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete s;
+}
+
+mpk::StreamArgs stream_args(const mp_stream *s) {
+    mpk::StreamArgs a{};
+    a.dist = s->dist == MP_DIST_EUCLID ? mpk::FIN_EUCLID : s->dist == MP_DIST_PNORM ? mpk::FIN_PNORM : mpk::FIN_ZNORM;
+    a.m = s->m;
+    a.excl = s->excl;
+    a.p = s->dist == MP_DIST_PNORM ? s->p : 2.0;
+    a.x = s->x64;
+    a.state = s->state;
+    a.R = s->R;
+    a.P = s->P;
+    a.I = reinterpret_cast<long long *>(s->I);
+    a.mu = s->mu;
+    a.S = s->S;
+    a.flat = s->flat;
+    a.part_r = s->part_r;
+    a.part_k = s->part_k;
+    a.counter = s->counter;
+    return a;
+}
+
+template <typename Tin>
+void stream_convert(const void *T, long long count, double *out, cudaStream_t st) {
+    mpk::convert_f64_kernel<Tin><<<grid_for(count, mpk::PREP_NT), mpk::PREP_NT, 0, st>>>(
+        static_cast<const Tin *>(T), count, count, out);
+    counted();
+}
+
+}  // namespace
+
+extern "C" {
+
+mp_status mp_stream_create(int dist, const void *T, int dtype, int64_t n, int64_t n_max, int32_t m, int64_t excl,
+                           double p, const mp_options *opt, mp_stream **out, void *stream) {
+    g_err[0] = 0;
+    if (!out) return fail(MP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (dist < MP_DIST_EUCLID || dist > MP_DIST_ZNORM) return fail(MP_ERR_INVALID_ARG, "dist %d", dist);
+    if (n_max < n) return fail(MP_ERR_INVALID_ARG, "n_max = %lld < n = %lld", (long long)n_max, (long long)n);
+    if (opt && opt->struct_size == sizeof(mp_options) && (opt->k_begin != 0 || opt->k_end != 0))
+        return fail(MP_ERR_UNSUPPORTED, "a streaming profile covers every diagonal");
+    Problem pb{};
+    pb.dist = dist;
+    pb.dtype = dtype;
+    pb.n = n;
+    pb.m = m;
+    pb.excl = excl;
+    pb.p = dist == MP_DIST_PNORM ? p : 2.0;
+    // the full argument check of the one-shot entry points (pointers P, I are checked later)
+    static const double dummy[1] = {0};
+    mp_status s = check_problem(pb, T, dummy, reinterpret_cast<const int64_t *>(dummy), opt);
+    if (s != MP_OK) return s;
+    if (n_max - m + 1 >= (1ll << 31) - 1) return fail(MP_ERR_UNSUPPORTED, "n_max too large");
+    if (pb.opt.reanchor < 0) return fail(MP_ERR_INVALID_ARG, "reanchor < 0");
+
+    auto *sp = new mp_stream();
+    sp->dist = dist;
+    sp->m = m;
+    sp->excl = excl;
+    sp->p = pb.p;
+    sp->n = n;
+    sp->N = n - m + 1;
+    sp->n_max = n_max;
+    sp->N_max = n_max - m + 1;
+    sp->reanchor = pb.opt.reanchor > 0 ? pb.opt.reanchor : 256;  // as the FP64 sweep's default
+    const size_t Nm = static_cast<size_t>(sp->N_max);
+    const size_t parts = (Nm + mpk::ST_NT - 1) / mpk::ST_NT + 1;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGetDevice(&sp->device);
+    if (e == cudaSuccess) e = cudaMalloc(&sp->x64, sizeof(double) * n_max);
+    if (e == cudaSuccess) e = cudaMalloc(&sp->state, sizeof(double) * Nm);
+    if (e == cudaSuccess) e = cudaMalloc(&sp->R, sizeof(double) * Nm);
+    if (e == cudaSuccess) e = cudaMalloc(&sp->P, sizeof(double) * Nm);
+    if (e == cudaSuccess) e = cudaMalloc(&sp->I, sizeof(long long) * Nm);
+    if (e == cudaSuccess) e = cudaMalloc(&sp->part_r, sizeof(double) * parts);
+    if (e == cudaSuccess) e = cudaMalloc(&sp->part_k, sizeof(long long) * parts);
+    if (e == cudaSuccess) e = cudaMalloc(&sp->counter, sizeof(unsigned));
+    if (e == cudaSuccess && dist == MP_DIST_ZNORM) {
+        e = cudaMalloc(&sp->mu, sizeof(double) * Nm);
+        if (e == cudaSuccess) e = cudaMalloc(&sp->S, sizeof(double) * Nm);
+        if (e == cudaSuccess) e = cudaMalloc(&sp->flat, Nm);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(sp->counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) {
+        stream_free(sp);
+        return cuda_fail(e, "allocating the streaming profile");
+    }
+    // the initial profile: the one-shot path (its workspace lives for this call only)
+    mp_options o = pb.opt;
+    o.polish = 1;
+    const Layout L = layout(pb);
+    void *ws = nullptr;
+    e = cudaMallocAsync(&ws, L.total, st);
+    if (e != cudaSuccess) {
+        stream_free(sp);
+        return cuda_fail(e, "allocating the initial workspace");
+    }
+    s = run(pb, T, sp->P, reinterpret_cast<int64_t *>(sp->I), ws, L.total, &o, stream);
+    cudaFreeAsync(ws, st);
+    if (s != MP_OK) {
+        cudaStreamSynchronize(st);
+        stream_free(sp);
+        return s;
+    }
+    if (dtype == MP_F64) stream_convert<double>(T, n, sp->x64, st);
+    else stream_convert<float>(T, n, sp->x64, st);
+    const mpk::StreamArgs a = stream_args(sp);
+    if (dist == MP_DIST_ZNORM) {
+        mpk::window_stats_kernel<<<grid_for(sp->N, mpk::PREP_NT), mpk::PREP_NT, 0, st>>>(sp->x64, sp->N, m, sp->mu,
+                                                                                        sp->S, sp->flat);
+        counted();
+    }
+    mpk::stream_rescore_kernel<<<grid_for(sp->N, mpk::ST_NT), mpk::ST_NT, 0, st>>>(a, sp->N);
+    mpk::stream_state_kernel<<<grid_for(sp->N, mpk::ST_NT), mpk::ST_NT, 0, st>>>(a, sp->N, excl + 1);
+    counted(2);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        stream_free(sp);
+        return cuda_fail(e, "initialising the streaming profile");
+    }
+    *out = sp;
+    return MP_OK;
+}
+
+mp_status mp_stream_append(mp_stream *sp, const void *x, int dtype, int64_t count, void *stream) {
+    g_err[0] = 0;
+    if (!sp) return fail(MP_ERR_INVALID_ARG, "stream is NULL");
+    if (count < 0) return fail(MP_ERR_INVALID_ARG, "count < 0");
+    if (count == 0) return MP_OK;
+    if (!x) return fail(MP_ERR_INVALID_ARG, "x is NULL");
+    if (dtype != MP_F32 && dtype != MP_F64) return fail(MP_ERR_INVALID_ARG, "dtype %d", dtype);
+    if (!aligned(x, dtype == MP_F64 ? 8 : 4)) return fail(MP_ERR_INVALID_ARG, "misaligned x");
+    if (sp->n + count > sp->n_max)
+        return fail(MP_ERR_UNSUPPORTED, "append of %lld samples exceeds the capacity (%lld of %lld used)",
+                    (long long)count, sp->n, sp->n_max);
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != sp->device) return fail(MP_ERR_INVALID_ARG, "stream made on device %d, current %d", sp->device, dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaGetLastError();
+    if (dtype == MP_F64) stream_convert<double>(x, count, sp->x64 + sp->n, st);
+    else stream_convert<float>(x, count, sp->x64 + sp->n, st);
+    const mpk::StreamArgs a = stream_args(sp);
+    for (long long t = 0; t < count; ++t) {
+        const long long j = sp->N;  // the new window
+        if (sp->dist == MP_DIST_ZNORM) {
+            mpk::stream_window_kernel<<<1, 32, 0, st>>>(a, j);
+            counted();
+        }
+        const long long cand = j - sp->excl;  // diagonals excl + 1 .. j
+        const unsigned blocks = static_cast<unsigned>(cand > 0 ? (cand + mpk::ST_NT - 1) / mpk::ST_NT : 1);
+        mpk::stream_step_kernel<<<blocks, mpk::ST_NT, 0, st>>>(a, j);
+        counted();
+        sp->n += 1;
+        sp->N += 1;
+        if (++sp->since_anchor >= sp->reanchor) {  // the diagonals' state again from the definitions
+            mpk::stream_state_kernel<<<grid_for(sp->N, mpk::ST_NT), mpk::ST_NT, 0, st>>>(a, sp->N, sp->excl + 1);
+            counted();
+            sp->since_anchor = 0;
+        }
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "append");
+    return MP_OK;
+}
+
+mp_status mp_stream_read(const mp_stream *sp, double *P, int64_t *I, void *stream) {
+    g_err[0] = 0;
+    if (!sp || !P || !I) return fail(MP_ERR_INVALID_ARG, "NULL stream, P or I");
+    if (!aligned(P, 8) || !aligned(I, 8)) return fail(MP_ERR_INVALID_ARG, "misaligned P or I");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(P, sp->P, sizeof(double) * sp->N, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(I, sp->I, sizeof(long long) * sp->N, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the streaming profile");
+    return MP_OK;
+}
+
+int64_t mp_stream_windows(const mp_stream *sp) { return sp ? sp->N : -1; }
+
+mp_status mp_stream_destroy(mp_stream *sp) {
+    stream_free(sp);
     return MP_OK;
 }
 

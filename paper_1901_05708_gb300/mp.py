@@ -10,6 +10,8 @@ be loaded, every call raises.
     P, I = acamp(T, m, excl)           # z-normalised     (Algorithm 2)
     plan = BatchPlan(lengths, ms, dists, excls)   # many series, one graph
     P, I = plan.run(T_concat)
+    st = StreamProfile(T, m, excl, n_max=...)     # append samples, profile kept exact
+    st.append(x); P, I = st.read()
 
 T is a 1-D float32/float64 CUDA tensor; P (float64) and I (int64) come back
 on the same device.  Calls are asynchronous on the current torch stream.
@@ -31,7 +33,8 @@ MP_DIST_EUCLID, MP_DIST_PNORM, MP_DIST_ZNORM = 0, 1, 2
 EXPORTS = ("mp_options_default", "mp_workspace_size", "mp_aamp", "mp_pnorm", "mp_acamp",
            "mp_sync_status", "mp_last_error", "mp_status_string", "mp_version", "mp_launch_count",
            "mp_set_sweep_events", "mp_aamp_noalloc", "mp_batch_plan_create", "mp_batch_run",
-           "mp_batch_windows", "mp_batch_tiles", "mp_batch_plan_destroy")
+           "mp_batch_windows", "mp_batch_tiles", "mp_batch_plan_destroy", "mp_stream_create",
+           "mp_stream_append", "mp_stream_read", "mp_stream_windows", "mp_stream_destroy")
 
 
 class MPError(RuntimeError):
@@ -106,6 +109,17 @@ def load(path: str | None = None):
         lib.mp_batch_tiles.restype = i64
         lib.mp_batch_plan_destroy.argtypes = [vp]
         lib.mp_batch_plan_destroy.restype = ctypes.c_int
+        lib.mp_stream_create.argtypes = [ctypes.c_int, vp, ctypes.c_int, i64, i64, i32, i64, d, opt_p,
+                                         ctypes.POINTER(vp), vp]
+        lib.mp_stream_create.restype = ctypes.c_int
+        lib.mp_stream_append.argtypes = [vp, vp, ctypes.c_int, i64, vp]
+        lib.mp_stream_append.restype = ctypes.c_int
+        lib.mp_stream_read.argtypes = [vp, vp, vp, vp]
+        lib.mp_stream_read.restype = ctypes.c_int
+        lib.mp_stream_windows.argtypes = [vp]
+        lib.mp_stream_windows.restype = i64
+        lib.mp_stream_destroy.argtypes = [vp]
+        lib.mp_stream_destroy.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -312,3 +326,60 @@ class BatchPlan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class StreamProfile:
+    """A matrix profile kept current while samples are appended (mp_stream_*).
+
+    StreamProfile(T, m, excl, dist='euclid', p=2.0, n_max=None) computes the
+    profile of T (1-D CUDA tensor) with room for n_max samples in all;
+    append(x) adds samples (a CUDA tensor), read() returns (P, I) of the
+    series so far."""
+
+    def __init__(self, T, m: int, excl: int, dist="euclid", p: float = 2.0, n_max: int | None = None,
+                 precision: str = "fp32", reanchor: int = 0, stream=None):
+        lib = load()
+        T, dtype = _prep(T)
+        self.device = T.device
+        n = T.numel()
+        n_max = n if n_max is None else int(n_max)
+        code = _DIST_CODES.get(dist, dist) if isinstance(dist, str) else int(dist)
+        opt = options(precision, reanchor, True)
+        h = ctypes.c_void_p()
+        s = stream if stream is not None else torch.cuda.current_stream(T.device)
+        _check(lib.mp_stream_create(code, ctypes.c_void_p(T.data_ptr()), dtype, n, n_max, m, excl, float(p),
+                                    ctypes.byref(opt), ctypes.byref(h), ctypes.c_void_p(s.cuda_stream)))
+        self._h = h
+        self._keep = T  # the input must outlive the asynchronous initial profile
+
+    @property
+    def windows(self) -> int:
+        return int(load().mp_stream_windows(self._h))
+
+    def append(self, x, stream=None):
+        x, dtype = _prep(x)
+        s = stream if stream is not None else torch.cuda.current_stream(x.device)
+        _check(load().mp_stream_append(self._h, ctypes.c_void_p(x.data_ptr()), dtype, x.numel(),
+                                       ctypes.c_void_p(s.cuda_stream)))
+        self._keep = x
+
+    def read(self, stream=None):
+        N = self.windows
+        P = torch.empty(N, dtype=torch.float64, device=self.device)
+        I = torch.empty(N, dtype=torch.int64, device=self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        _check(load().mp_stream_read(self._h, ctypes.c_void_p(P.data_ptr()), ctypes.c_void_p(I.data_ptr()),
+                                     ctypes.c_void_p(s.cuda_stream)))
+        return P, I
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            torch.cuda.synchronize(self.device)
+            load().mp_stream_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

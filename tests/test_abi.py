@@ -132,6 +132,34 @@ def test_batch_checks_need_no_gpu(lib):
     assert lib.mp_batch_plan_destroy(None) == E.MP_OK
 
 
+def test_stream_checks_need_no_gpu(lib):
+    """mp_stream_create rejects bad arguments before any CUDA call."""
+    E = mp
+    vp = ctypes.c_void_p
+
+    def create(dist=0, T=0x1000, dtype=0, n=100, n_max=200, m=10, excl=2, p=2.0, opt=None):
+        h = vp()
+        st = lib.mp_stream_create(dist, vp(T), dtype, n, n_max, m, excl, p, ctypes.byref(opt) if opt else None,
+                                  ctypes.byref(h), vp(0))
+        assert not h.value
+        return st
+
+    assert create(dist=5) == E.MP_ERR_INVALID_ARG
+    assert create(n_max=50) == E.MP_ERR_INVALID_ARG         # n_max < n
+    assert create(m=101) == E.MP_ERR_INVALID_ARG            # m > n
+    assert create(T=0) == E.MP_ERR_INVALID_ARG
+    assert create(dist=2, m=1) == E.MP_ERR_INVALID_ARG      # z-normalised with m = 1
+    assert create(dist=1, p=0.5) == E.MP_ERR_INVALID_ARG
+    o = mp.Options()
+    lib.mp_options_default(ctypes.byref(o))
+    o.k_begin = 3
+    assert create(opt=o) == E.MP_ERR_UNSUPPORTED
+    assert lib.mp_stream_append(None, vp(0x1000), 0, 1, vp(0)) == E.MP_ERR_INVALID_ARG
+    assert lib.mp_stream_read(None, vp(0x1000), vp(0x2000), vp(0)) == E.MP_ERR_INVALID_ARG
+    assert lib.mp_stream_windows(None) == -1
+    assert lib.mp_stream_destroy(None) == E.MP_OK
+
+
 def test_binding_refuses_cpu_tensors(lib):
     torch = pytest.importorskip("torch")
     with pytest.raises(TypeError):
