@@ -280,6 +280,48 @@ int64_t mp_stream_windows(const mp_stream *s);
 /* Free the stream's device memory (after its last append has completed). */
 mp_status mp_stream_destroy(mp_stream *s);
 
+/* ---- Anytime runs: a profile that improves tile by tile ---------------------
+ *
+ * The paper's algorithms can be stopped early (Sec. 1 mentions the anytime
+ * use of the incremental formulation): every cell already evaluated is exact,
+ * so the profile of any subset of diagonals is an upper bound that tightens
+ * towards the final one.  An anytime run takes one float32 series, splits it
+ * into the batch path's tiles, orders them by a seeded random permutation and
+ * evaluates the next tiles of that order on each mp_anytime_run call; between
+ * calls mp_anytime_read gives the profile of the cells done so far (rows
+ * without a candidate yet: P = +inf, I = -1), and the keys with the queue
+ * cursor can be saved to and restored from host memory.  When every tile has
+ * run, P and I equal the batch path's result for the series exactly.
+ */
+typedef struct mp_anytime mp_anytime;
+
+/* T: device, n float32 samples (copied; T may be freed after the call).
+ * seed != 0 fixes the tile order (0 selects a built-in seed).  opt as for a
+ * batch (FP32 sweep, polish honoured).  Errors: as mp_batch_plan_create. */
+mp_status mp_anytime_create(int dist, const void *T, int64_t n, int32_t m, int64_t excl, double p,
+                            uint64_t seed, const mp_options *opt, mp_anytime **out, void *stream);
+
+/* Evaluate the next min(max_tiles, remaining) tiles (asynchronous). */
+mp_status mp_anytime_run(mp_anytime *a, int64_t max_tiles, void *stream);
+
+/* P, I (device, N entries) of every cell evaluated so far. */
+mp_status mp_anytime_read(const mp_anytime *a, double *P, int64_t *I, void *stream);
+
+/* Tiles evaluated so far / in all, or -1 for NULL. */
+int64_t mp_anytime_tiles_done(const mp_anytime *a);
+int64_t mp_anytime_tiles_total(const mp_anytime *a);
+
+/* Checkpoint: a header (magic, seed, N, cursor) and the N profile keys, in
+ * host memory of mp_anytime_checkpoint_size() bytes; the key copy is
+ * asynchronous on `stream`.  mp_anytime_restore loads one into an anytime run
+ * of the same series, seed and size (else MP_ERR_INVALID_ARG). */
+size_t mp_anytime_checkpoint_size(const mp_anytime *a);
+mp_status mp_anytime_checkpoint(const mp_anytime *a, void *host, size_t bytes, void *stream);
+mp_status mp_anytime_restore(mp_anytime *a, const void *host, size_t bytes, void *stream);
+
+/* Free the run (after its last call has completed). */
+mp_status mp_anytime_destroy(mp_anytime *a);
+
 #ifdef __cplusplus
 }
 #endif

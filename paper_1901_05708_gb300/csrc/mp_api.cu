@@ -817,11 +817,35 @@ mp_status batch_build_graph(mp_batch_plan *pl, const void *T, double *P, int64_t
 
 }  // namespace
 
+static mp_status batch_plan_build(const mp_batch_desc *desc, const mp_options *opt, unsigned long long seed,
+                                  mp_batch_plan **plan, size_t *ws_bytes);
+
 extern "C" {
 
 mp_status mp_batch_plan_create(const mp_batch_desc *desc, const mp_options *opt, mp_batch_plan **plan,
                                size_t *ws_bytes) {
     g_err[0] = 0;
+    return batch_plan_build(desc, opt, 0, plan, ws_bytes);
+}
+
+}  // extern "C"
+
+namespace {
+
+// splitmix64: a small counter-based generator, the same sequence on every platform
+unsigned long long splitmix64(unsigned long long &x) {
+    unsigned long long z = (x += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+// Build a plan; seed = 0 orders every tile queue by decreasing cost (longest
+// first), another seed by a seeded random permutation (anytime runs).
+static mp_status batch_plan_build(const mp_batch_desc *desc, const mp_options *opt, unsigned long long seed,
+                                  mp_batch_plan **plan, size_t *ws_bytes) {
     if (!plan) return fail(MP_ERR_INVALID_ARG, "plan is NULL");
     *plan = nullptr;
     mp_options o{};
@@ -889,9 +913,16 @@ mp_status mp_batch_plan_create(const mp_batch_desc *desc, const mp_options *opt,
             batch_free(pl);
             return fail(MP_ERR_UNSUPPORTED, "more than 2^32 - 2 tiles in one queue");
         }
-        // longest tiles first; ties in series / band / row order
-        std::stable_sort(q[qi].begin(), q[qi].end(),
-                         [](const auto &a, const auto &b) { return a.first > b.first; });
+        if (seed == 0) {  // longest tiles first; ties in series / band / row order
+            std::stable_sort(q[qi].begin(), q[qi].end(),
+                             [](const auto &a, const auto &b) { return a.first > b.first; });
+        } else {  // Fisher-Yates with splitmix64
+            unsigned long long st = seed ^ (0x632be59bd9b4e019ull * (qi + 1));
+            for (size_t t = q[qi].size(); t > 1; --t) {
+                const size_t r = static_cast<size_t>(splitmix64(st) % t);
+                std::swap(q[qi][t - 1], q[qi][r]);
+            }
+        }
         pl->tiles[qi].reserve(q[qi].size());
         for (auto &t : q[qi]) pl->tiles[qi].push_back(t.second);
         if (qi == mp_batch_plan::Q_FAST2 || qi == mp_batch_plan::Q_FASTP)
@@ -960,6 +991,8 @@ mp_status mp_batch_plan_create(const mp_batch_desc *desc, const mp_options *opt,
     if (ws_bytes) *ws_bytes = pl->ws_bytes;
     return MP_OK;
 }
+
+extern "C" {
 
 mp_status mp_batch_run(mp_batch_plan *plan, const void *T, double *P, int64_t *I, void *ws, size_t ws_bytes,
                        void *stream) {
@@ -1212,6 +1245,229 @@ int64_t mp_stream_windows(const mp_stream *sp) { return sp ? sp->N : -1; }
 
 mp_status mp_stream_destroy(mp_stream *sp) {
     stream_free(sp);
+    return MP_OK;
+}
+
+}  // extern "C"
+
+// ---- anytime runs ---------------------------------------------------------------------
+// One series, its tiles in a seeded random order; each run takes the next
+// tiles of the queue, and the profile of the cells done so far can be read
+// (and the keys checkpointed) between runs.
+struct mp_anytime {
+    mp_batch_plan *pl = nullptr;
+    void *ws = nullptr;
+    float *T = nullptr;            // the library's copy of the series
+    int qi = -1;                   // the queue that holds the series' tiles
+    long long cursor = 0, total = 0;
+    unsigned long long seed = 0;
+    bool started = false;
+};
+
+namespace {
+
+constexpr unsigned long long ANYTIME_MAGIC = 0x4d50616e7974696dull;  // "MPanytim"
+
+void anytime_free(mp_anytime *a) {
+    if (!a) return;
+    if (a->pl) batch_free(a->pl);
+    if (a->ws) cudaFree(a->ws);
+    if (a->T) cudaFree(a->T);
+    delete a;
+}
+
+mpk::BatchData anytime_data(const mp_anytime *a, double *P, int64_t *I) {
+    const mp_batch_plan *pl = a->pl;
+    char *w = static_cast<char *>(a->ws);
+    mpk::BatchData bd{};
+    bd.series = pl->d_series;
+    bd.w_start = pl->d_wstart;
+    bd.S = pl->S;
+    bd.windows = pl->windows;
+    bd.T = a->T;
+    bd.keys = reinterpret_cast<unsigned long long *>(w + pl->o_keys);
+    if (pl->zwindows > 0) {
+        bd.mu = reinterpret_cast<double *>(w + pl->o_mu);
+        bd.Sx = reinterpret_cast<double *>(w + pl->o_S);
+        bd.flat = reinterpret_cast<unsigned char *>(w + pl->o_flat);
+        bd.df = reinterpret_cast<float *>(w + pl->o_df);
+        bd.dg = reinterpret_cast<float *>(w + pl->o_dg);
+        bd.inv = reinterpret_cast<float *>(w + pl->o_inv);
+        bd.muh = reinterpret_cast<float *>(w + pl->o_muh);
+        bd.mul = reinterpret_cast<float *>(w + pl->o_mul);
+    }
+    bd.P = P;
+    bd.I = reinterpret_cast<long long *>(I);
+    bd.p = pl->p;
+    bd.polish = pl->polish;
+    return bd;
+}
+
+// keys <- none, tickets <- 0, z statistics (once per object)
+void anytime_start(mp_anytime *a, cudaStream_t st) {
+    const mp_batch_plan *pl = a->pl;
+    const mpk::BatchData bd = anytime_data(a, nullptr, nullptr);
+    unsigned *tickets = reinterpret_cast<unsigned *>(static_cast<char *>(a->ws) + pl->o_tickets);
+    const int gw = grid_for(pl->windows, mpk::PREP_NT);
+    mpk::batch_init_kernel<<<gw, mpk::PREP_NT, 0, st>>>(bd.keys, pl->windows, tickets, mp_batch_plan::NQ);
+    counted();
+    if (pl->zwindows > 0) {
+        mpk::batch_zstats_kernel<<<gw, mpk::PREP_NT, 0, st>>>(bd);
+        mpk::batch_zoperands_kernel<<<gw, mpk::PREP_NT, 0, st>>>(bd);
+        counted(2);
+    }
+    a->started = true;
+}
+
+}  // namespace
+
+extern "C" {
+
+mp_status mp_anytime_create(int dist, const void *T, int64_t n, int32_t m, int64_t excl, double p,
+                            uint64_t seed, const mp_options *opt, mp_anytime **out, void *stream) {
+    g_err[0] = 0;
+    if (!out) return fail(MP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!T) return fail(MP_ERR_INVALID_ARG, "T is NULL");
+    if (!aligned(T, 4)) return fail(MP_ERR_INVALID_ARG, "misaligned T");
+    if (dist < MP_DIST_EUCLID || dist > MP_DIST_ZNORM) return fail(MP_ERR_INVALID_ARG, "dist %d", dist);
+    const int64_t offs[2] = {0, n};
+    const int32_t ms[1] = {m};
+    const uint8_t ds[1] = {static_cast<uint8_t>(dist)};
+    const int64_t ex[1] = {excl};
+    mp_batch_desc d{};
+    d.struct_size = sizeof(mp_batch_desc);
+    d.num_series = 1;
+    d.t_offsets = offs;
+    d.m = ms;
+    d.dist = ds;
+    d.excl = ex;
+    d.p = p;
+    d.dtype = MP_F32;
+    auto *a = new mp_anytime();
+    a->seed = seed ? seed : 0x5eed5eed5eedull;
+    size_t ws = 0;
+    mp_status s = batch_plan_build(&d, opt, a->seed, &a->pl, &ws);
+    if (s != MP_OK) {
+        delete a;
+        return s;
+    }
+    for (int qi = 0; qi < mp_batch_plan::NQ; ++qi)
+        if (!a->pl->tiles[qi].empty()) a->qi = qi;
+    a->total = a->qi < 0 ? 0 : static_cast<long long>(a->pl->tiles[a->qi].size());
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMalloc(&a->ws, ws);
+    if (e == cudaSuccess) e = cudaMalloc(&a->T, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(a->T, T, sizeof(float) * n, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) {
+        anytime_free(a);
+        return cuda_fail(e, "allocating the anytime run");
+    }
+    anytime_start(a, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        anytime_free(a);
+        return cuda_fail(e, "starting the anytime run");
+    }
+    *out = a;
+    return MP_OK;
+}
+
+mp_status mp_anytime_run(mp_anytime *a, int64_t max_tiles, void *stream) {
+    g_err[0] = 0;
+    if (!a) return fail(MP_ERR_INVALID_ARG, "anytime run is NULL");
+    if (max_tiles < 0) return fail(MP_ERR_INVALID_ARG, "max_tiles < 0");
+    const long long count = std::min<long long>(max_tiles, a->total - a->cursor);
+    if (count <= 0) return MP_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaGetLastError();
+    mp_batch_plan *pl = a->pl;
+    const int qi = a->qi;
+    unsigned *ticket = reinterpret_cast<unsigned *>(static_cast<char *>(a->ws) + pl->o_tickets) + qi;
+    cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return cuda_fail(e, "resetting the queue ticket");
+    const mpk::BatchData bd = anytime_data(a, nullptr, nullptr);
+    const mpk::BatchQueue q{pl->d_tiles[qi] + a->cursor, static_cast<unsigned>(count), ticket};
+    const int grid = static_cast<int>(std::min<long long>(pl->grid[qi], count));
+    if (qi == mp_batch_plan::Q_FAST2)
+        mpk::sweep2_batch_kernel<mpk::K_P2><<<grid, mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
+    else if (qi == mp_batch_plan::Q_FASTP && pl->genp_kind == mpk::K_P1)
+        mpk::sweep2_batch_kernel<mpk::K_P1><<<grid, mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
+    else if (qi == mp_batch_plan::Q_FASTP)
+        mpk::sweep2_batch_kernel<mpk::K_P3><<<grid, mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
+    else if (qi == mp_batch_plan::Q_Z)
+        mpk::sweepz_batch_kernel<<<grid, mpk::Z_NT, pl->smem[qi], st>>>(bd, q);
+    else {
+        const int saved = pl->grid[qi];  // launch_gen_batch takes the grid from the plan
+        pl->grid[qi] = grid;
+        gen_dispatch_launch(pl, bd, q, qi, qi == mp_batch_plan::Q_GEN2 ? mpk::K_P2 : pl->genp_kind, st);
+        pl->grid[qi] = saved;
+    }
+    counted();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "anytime sweep launch");
+    a->cursor += count;
+    return MP_OK;
+}
+
+mp_status mp_anytime_read(const mp_anytime *a, double *P, int64_t *I, void *stream) {
+    g_err[0] = 0;
+    if (!a || !P || !I) return fail(MP_ERR_INVALID_ARG, "NULL anytime run, P or I");
+    if (!aligned(P, 8) || !aligned(I, 8)) return fail(MP_ERR_INVALID_ARG, "misaligned P or I");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const mpk::BatchData bd = anytime_data(a, P, I);
+    mpk::batch_finalize_kernel<<<grid_for(a->pl->windows, mpk::PREP_NT), mpk::PREP_NT, 0, st>>>(bd);
+    counted();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "anytime finalize");
+    return MP_OK;
+}
+
+int64_t mp_anytime_tiles_done(const mp_anytime *a) { return a ? a->cursor : -1; }
+
+int64_t mp_anytime_tiles_total(const mp_anytime *a) { return a ? a->total : -1; }
+
+size_t mp_anytime_checkpoint_size(const mp_anytime *a) {
+    return a ? 4 * sizeof(unsigned long long) + sizeof(unsigned long long) * a->pl->windows : 0;
+}
+
+mp_status mp_anytime_checkpoint(const mp_anytime *a, void *host, size_t bytes, void *stream) {
+    g_err[0] = 0;
+    if (!a || !host) return fail(MP_ERR_INVALID_ARG, "NULL anytime run or buffer");
+    if (bytes < mp_anytime_checkpoint_size(a))
+        return fail(MP_ERR_INVALID_ARG, "checkpoint buffer %zu bytes < %zu", bytes, mp_anytime_checkpoint_size(a));
+    unsigned long long *h = static_cast<unsigned long long *>(host);
+    h[0] = ANYTIME_MAGIC;
+    h[1] = a->seed;
+    h[2] = static_cast<unsigned long long>(a->pl->windows);
+    h[3] = static_cast<unsigned long long>(a->cursor);
+    const void *keys = static_cast<const char *>(a->ws) + a->pl->o_keys;
+    const cudaError_t e = cudaMemcpyAsync(h + 4, keys, sizeof(unsigned long long) * a->pl->windows,
+                                          cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "checkpoint copy");
+    return MP_OK;
+}
+
+mp_status mp_anytime_restore(mp_anytime *a, const void *host, size_t bytes, void *stream) {
+    g_err[0] = 0;
+    if (!a || !host) return fail(MP_ERR_INVALID_ARG, "NULL anytime run or buffer");
+    if (bytes < mp_anytime_checkpoint_size(a))
+        return fail(MP_ERR_INVALID_ARG, "checkpoint buffer %zu bytes < %zu", bytes, mp_anytime_checkpoint_size(a));
+    const unsigned long long *h = static_cast<const unsigned long long *>(host);
+    if (h[0] != ANYTIME_MAGIC || h[1] != a->seed || h[2] != static_cast<unsigned long long>(a->pl->windows) ||
+        h[3] > static_cast<unsigned long long>(a->total))
+        return fail(MP_ERR_INVALID_ARG, "checkpoint does not belong to this series, seed and size");
+    void *keys = static_cast<char *>(a->ws) + a->pl->o_keys;
+    const cudaError_t e = cudaMemcpyAsync(keys, h + 4, sizeof(unsigned long long) * a->pl->windows,
+                                          cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "restore copy");
+    a->cursor = static_cast<long long>(h[3]);
+    return MP_OK;
+}
+
+mp_status mp_anytime_destroy(mp_anytime *a) {
+    anytime_free(a);
     return MP_OK;
 }
 

@@ -34,7 +34,10 @@ EXPORTS = ("mp_options_default", "mp_workspace_size", "mp_aamp", "mp_pnorm", "mp
            "mp_sync_status", "mp_last_error", "mp_status_string", "mp_version", "mp_launch_count",
            "mp_set_sweep_events", "mp_aamp_noalloc", "mp_batch_plan_create", "mp_batch_run",
            "mp_batch_windows", "mp_batch_tiles", "mp_batch_plan_destroy", "mp_stream_create",
-           "mp_stream_append", "mp_stream_read", "mp_stream_windows", "mp_stream_destroy")
+           "mp_stream_append", "mp_stream_read", "mp_stream_windows", "mp_stream_destroy",
+           "mp_anytime_create", "mp_anytime_run", "mp_anytime_read", "mp_anytime_tiles_done",
+           "mp_anytime_tiles_total", "mp_anytime_checkpoint_size", "mp_anytime_checkpoint",
+           "mp_anytime_restore", "mp_anytime_destroy")
 
 
 class MPError(RuntimeError):
@@ -120,6 +123,25 @@ def load(path: str | None = None):
         lib.mp_stream_windows.restype = i64
         lib.mp_stream_destroy.argtypes = [vp]
         lib.mp_stream_destroy.restype = ctypes.c_int
+        lib.mp_anytime_create.argtypes = [ctypes.c_int, vp, i64, i32, i64, d, ctypes.c_uint64, opt_p,
+                                          ctypes.POINTER(vp), vp]
+        lib.mp_anytime_create.restype = ctypes.c_int
+        lib.mp_anytime_run.argtypes = [vp, i64, vp]
+        lib.mp_anytime_run.restype = ctypes.c_int
+        lib.mp_anytime_read.argtypes = [vp, vp, vp, vp]
+        lib.mp_anytime_read.restype = ctypes.c_int
+        lib.mp_anytime_tiles_done.argtypes = [vp]
+        lib.mp_anytime_tiles_done.restype = i64
+        lib.mp_anytime_tiles_total.argtypes = [vp]
+        lib.mp_anytime_tiles_total.restype = i64
+        lib.mp_anytime_checkpoint_size.argtypes = [vp]
+        lib.mp_anytime_checkpoint_size.restype = sz
+        lib.mp_anytime_checkpoint.argtypes = [vp, vp, sz, vp]
+        lib.mp_anytime_checkpoint.restype = ctypes.c_int
+        lib.mp_anytime_restore.argtypes = [vp, vp, sz, vp]
+        lib.mp_anytime_restore.restype = ctypes.c_int
+        lib.mp_anytime_destroy.argtypes = [vp]
+        lib.mp_anytime_destroy.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -376,6 +398,78 @@ class StreamProfile:
         if getattr(self, "_h", None) is not None and self._h.value:
             torch.cuda.synchronize(self.device)
             load().mp_stream_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Anytime:
+    """An anytime matrix profile (mp_anytime_*): tiles in a seeded random order,
+    run(k) evaluates the next k tiles, read() gives the profile of the cells
+    done so far, checkpoint() / restore() save and load the progress."""
+
+    def __init__(self, T, m: int, excl: int, dist="euclid", p: float = 2.0, seed: int = 1, polish: bool = True,
+                 stream=None):
+        lib = load()
+        if not isinstance(T, torch.Tensor) or not T.is_cuda or T.dtype != torch.float32 or T.dim() != 1:
+            raise TypeError("T must be a 1-D float32 CUDA tensor")
+        T = T.contiguous()
+        self.device = T.device
+        self.N = T.numel() - m + 1
+        code = _DIST_CODES.get(dist, dist) if isinstance(dist, str) else int(dist)
+        opt = options(polish=polish)
+        h = ctypes.c_void_p()
+        s = stream if stream is not None else torch.cuda.current_stream(T.device)
+        _check(lib.mp_anytime_create(code, ctypes.c_void_p(T.data_ptr()), T.numel(), m, excl, float(p), int(seed),
+                                     ctypes.byref(opt), ctypes.byref(h), ctypes.c_void_p(s.cuda_stream)))
+        self._h = h
+        self._keep = T
+
+    @property
+    def tiles_done(self) -> int:
+        return int(load().mp_anytime_tiles_done(self._h))
+
+    @property
+    def tiles_total(self) -> int:
+        return int(load().mp_anytime_tiles_total(self._h))
+
+    def run(self, max_tiles: int, stream=None):
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        _check(load().mp_anytime_run(self._h, int(max_tiles), ctypes.c_void_p(s.cuda_stream)))
+
+    def read(self, stream=None):
+        P = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        I = torch.empty(self.N, dtype=torch.int64, device=self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        _check(load().mp_anytime_read(self._h, ctypes.c_void_p(P.data_ptr()), ctypes.c_void_p(I.data_ptr()),
+                                      ctypes.c_void_p(s.cuda_stream)))
+        return P, I
+
+    def checkpoint(self) -> bytes:
+        lib = load()
+        n = int(lib.mp_anytime_checkpoint_size(self._h))
+        buf = torch.empty(n, dtype=torch.uint8).pin_memory()
+        s = torch.cuda.current_stream(self.device)
+        _check(lib.mp_anytime_checkpoint(self._h, ctypes.c_void_p(buf.data_ptr()), n, ctypes.c_void_p(s.cuda_stream)))
+        torch.cuda.synchronize(self.device)
+        return bytes(buf.numpy().tobytes())
+
+    def restore(self, blob: bytes):
+        lib = load()
+        buf = torch.frombuffer(bytearray(blob), dtype=torch.uint8).pin_memory()
+        s = torch.cuda.current_stream(self.device)
+        _check(lib.mp_anytime_restore(self._h, ctypes.c_void_p(buf.data_ptr()), buf.numel(),
+                                      ctypes.c_void_p(s.cuda_stream)))
+        torch.cuda.synchronize(self.device)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            torch.cuda.synchronize(self.device)
+            load().mp_anytime_destroy(self._h)
             self._h = None
 
     def __del__(self):
