@@ -33,7 +33,7 @@ if ROOT not in sys.path:
 
 from paper_1901_05708_gb300 import workloads as W  # noqa: E402
 
-METRIC = "distance-matrix cells/s (AAMP FP32 sweep, re-anchored, FP64-polished P)"
+METRIC = "distance-matrix cells/s (GCells/s) at 1 GB300 + % FP32 roofline, FP32 vs FP64 sweep"
 UNIT = "GCells/s"
 FP32_INSTR_PER_CELL = 4          # minimum FP32-pipe instructions per cell (Lemma 1 update)
 FP32_LANES_PER_SM = 128
@@ -170,7 +170,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, len(runs)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config,
+            "data": "synthetic", "config": dict(config, precision="fp64 CPU oracle (OpenMP over diagonals)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": runs[0]["cores"], "kind": "oracle",
                              "sample": runs[0]["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
