@@ -68,13 +68,26 @@ typedef enum {
 
 typedef enum { MP_DIST_EUCLID = 0, MP_DIST_PNORM = 1, MP_DIST_ZNORM = 2 } mp_dist;
 
+/* Kernel of the FP32 Euclidean / p-norm sweep (the z-normalised distance has
+ * one FP32 kernel).  AUTO: the two-stream kernel where it applies (FP32
+ * input, m a multiple of 32, p in {1, 2, 3}, default re-anchor interval),
+ * with the block filter for p = 2 and N >= 200,000; else the generic kernel.
+ * The others force a choice (MP_ERR_UNSUPPORTED where it does not apply);
+ * mp_autotune times them. */
+typedef enum {
+    MP_VARIANT_AUTO = 0,
+    MP_VARIANT_FAST_FILTER = 1,  /* two-stream kernel with the block filter (p = 2) */
+    MP_VARIANT_FAST = 2,         /* two-stream kernel                               */
+    MP_VARIANT_GENERIC = 3       /* generic kernel (any m, p, input type; reanchor)  */
+} mp_variant;
+
 typedef struct mp_options {
     uint32_t struct_size; /* = sizeof(mp_options); set by mp_options_default      */
     int32_t precision;    /* mp_precision (default MP_PREC_FP32)                  */
     int32_t reanchor;     /* rows between exact re-anchors; 0 = chosen from m     */
     int32_t polish;       /* 1 (default): P[i] recomputed in FP64 as d(i, I[i])   */
                           /* 0: P is the sweep's own (FP32 or FP64) value          */
-    int32_t reserved0;
+    int32_t variant;      /* FP32 sweep kernel, mp_variant (default MP_VARIANT_AUTO) */
     int64_t k_begin;      /* sweep only diagonals k >= k_begin (default 0)        */
     int64_t k_end;        /* ... and k < k_end (<= 0 means no upper bound).       */
                           /* Disjoint ranges computed separately and merged with  */
@@ -321,6 +334,38 @@ mp_status mp_anytime_restore(mp_anytime *a, const void *host, size_t bytes, void
 
 /* Free the run (after its last call has completed). */
 mp_status mp_anytime_destroy(mp_anytime *a);
+
+/* ---- Autotuning -------------------------------------------------------------
+ *
+ * mp_autotune times the kernel variants that apply to a problem (for the
+ * generic kernel: its default re-anchor interval and intervals of 16, 32 and
+ * 64 rows that divide m into at most 8 blocks, each distinct interval once)
+ * on the caller's series, each candidate once to warm up and once timed (the
+ * sweep kernel alone, CUDA events on `stream`; the call synchronises it).
+ * slice_cells = 0 times the whole sweep; slice_cells > 0 only the first
+ * diagonals, about that many cells (faster, but thresholds stay as loose as at
+ * the start of a sweep, which understates the block filter).
+ * *best receives the fastest options (opt's other fields kept); times_ms, if
+ * not NULL, the times of the candidates in the order listed above (up to
+ * max_times entries, -1 for one that does not apply), and *n_times their
+ * number.  Results are cached in memory per (device name, dist, dtype, m,
+ * log2 N, p); a cached problem returns at once without timing (*n_times = 0)
+ * unless `force`.  P and I (N entries, device) are scratch for the timed runs;
+ * their content afterwards is unspecified.  Arguments and errors as mp_aamp /
+ * mp_pnorm / mp_acamp (ws sized by mp_workspace_size for opt). */
+mp_status mp_autotune(int dist, const void *T, int dtype, int64_t n, int32_t m, int64_t excl, double p,
+                      double *P, int64_t *I, void *ws, size_t ws_bytes, const mp_options *opt,
+                      int64_t slice_cells, int force, mp_options *best, double *times_ms,
+                      int32_t max_times, int32_t *n_times, void *stream);
+
+/* Save / load the autotuning cache as text, one entry per line.  Loading
+ * merges into the cache (entries of other devices are kept).  Errors:
+ * MP_ERR_INVALID_ARG (NULL path, unreadable or malformed file). */
+mp_status mp_autotune_cache_save(const char *path);
+mp_status mp_autotune_cache_load(const char *path);
+
+/* Entries in the cache. */
+int64_t mp_autotune_cache_size(void);
 
 #ifdef __cplusplus
 }

@@ -11,7 +11,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
 #include <utility>
 #include <vector>
 
@@ -138,6 +140,8 @@ mp_status check_problem(Problem &pb, const void *T, const double *P, const int64
         return fail(MP_ERR_INVALID_ARG, "precision %d", pb.opt.precision);
     if (pb.opt.reanchor < 0) return fail(MP_ERR_INVALID_ARG, "reanchor %d < 0", pb.opt.reanchor);
     if (pb.opt.polish != 0 && pb.opt.polish != 1) return fail(MP_ERR_INVALID_ARG, "polish %d", pb.opt.polish);
+    if (pb.opt.variant < MP_VARIANT_AUTO || pb.opt.variant > MP_VARIANT_GENERIC)
+        return fail(MP_ERR_INVALID_ARG, "variant %d", pb.opt.variant);
     if (pb.opt.k_begin < 0) return fail(MP_ERR_INVALID_ARG, "k_begin %lld < 0", (long long)pb.opt.k_begin);
     if (!T || !P || !I) return fail(MP_ERR_INVALID_ARG, "NULL T, P or I");
     if (!aligned(T, pb.dtype == MP_F64 ? 8 : 4) || !aligned(P, 8) || !aligned(I, 8))
@@ -224,10 +228,15 @@ int kind_of(int dist, double p) {
 // Fast two-stream path (f32x2 arithmetic, tagged minima): Euclidean or
 // p-norm with p in {1, 2, 3}, FP32 input, m a multiple of 32 (re-anchor every
 // m / 4 rows), default re-anchor interval, shared memory for two CTAs per SM.
-bool fast_path_ok(const Problem &pb) {
+bool fast_path_applies(const Problem &pb) {
     const bool lp = pb.dist == MP_DIST_EUCLID || (pb.dist == MP_DIST_PNORM && kind_of(pb.dist, pb.p) != mpk::K_PG);
     return lp && pb.dtype == MP_F32 && pb.m % 32 == 0 && pb.opt.reanchor == 0 &&
-           mpk::sweep2_smem_bytes(pb.m, mpk::V2_QMAX) <= mpk::V2_SMEM_MAX && !getenv_generic();
+           mpk::sweep2_smem_bytes(pb.m, mpk::V2_QMAX) <= mpk::V2_SMEM_MAX;
+}
+
+bool fast_path_ok(const Problem &pb) {
+    if (pb.opt.variant == MP_VARIANT_GENERIC) return false;
+    return fast_path_applies(pb) && !getenv_generic();
 }
 
 template <int KIND, bool FILTER>
@@ -268,9 +277,12 @@ mp_status run_sweep2(const Problem &pb, const Layout &L, char *ws, cudaStream_t 
     switch (kind_of(pb.dist, pb.p)) {
         case mpk::K_P1: return launch_sweep2_t<mpk::K_P1, false>(a, smem, st);
         case mpk::K_P3: return launch_sweep2_t<mpk::K_P3, false>(a, smem, st);
-        default:
-            return pb.N >= FILTER_MIN_N ? launch_sweep2_t<mpk::K_P2, true>(a, smem, st)
-                                        : launch_sweep2_t<mpk::K_P2, false>(a, smem, st);
+        default: {
+            const bool filter = pb.opt.variant == MP_VARIANT_FAST_FILTER ||
+                                (pb.opt.variant == MP_VARIANT_AUTO && pb.N >= FILTER_MIN_N);
+            return filter ? launch_sweep2_t<mpk::K_P2, true>(a, smem, st)
+                          : launch_sweep2_t<mpk::K_P2, false>(a, smem, st);
+        }
     }
 }
 
@@ -316,6 +328,14 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
               const mp_options *opt, void *stream) {
     mp_status s = check_problem(pb, T, P, I, opt);
     if (s != MP_OK) return s;
+    const int v = pb.opt.variant;
+    if ((v == MP_VARIANT_FAST || v == MP_VARIANT_FAST_FILTER) &&
+        (pb.opt.precision != MP_PREC_FP32 || pb.dist == MP_DIST_ZNORM || !fast_path_applies(pb)))
+        return fail(MP_ERR_UNSUPPORTED, "the two-stream kernel does not apply to this problem");
+    if (v == MP_VARIANT_FAST_FILTER && kind_of(pb.dist, pb.p) != mpk::K_P2)
+        return fail(MP_ERR_UNSUPPORTED, "the block filter exists for p = 2 only");
+    if (v == MP_VARIANT_GENERIC && (pb.opt.precision != MP_PREC_FP32 || pb.dist == MP_DIST_ZNORM))
+        return fail(MP_ERR_UNSUPPORTED, "the generic kernel is the FP32 Euclidean / p-norm sweep");
     const Layout L = layout(pb);
     if (!ws) return fail(MP_ERR_WORKSPACE, "workspace is NULL (need %zu bytes)", L.total);
     if (!aligned(ws, ALIGN)) return fail(MP_ERR_INVALID_ARG, "workspace not 256-byte aligned");
@@ -1469,6 +1489,202 @@ mp_status mp_anytime_restore(mp_anytime *a, const void *host, size_t bytes, void
 mp_status mp_anytime_destroy(mp_anytime *a) {
     anytime_free(a);
     return MP_OK;
+}
+
+}  // extern "C"
+
+// ---- autotuning -------------------------------------------------------------------
+namespace {
+
+struct TuneEntry {
+    int variant = 0, reanchor = 0;
+    double ms = 0;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneEntry> g_tune;
+
+std::string tune_key(int dist, int dtype, int m, long long N, double p) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    std::string name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "unknown";
+    for (char &c : name)
+        if (c == ' ' || c == '|') c = '_';
+    int lg = 0;
+    while ((2LL << lg) <= N) ++lg;
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|%d|%d|%d|%d|%.6g", name.c_str(), dist, dtype, m, lg,
+             dist == MP_DIST_PNORM ? p : 2.0);
+    return buf;
+}
+
+}  // namespace
+
+extern "C" {
+
+mp_status mp_autotune(int dist, const void *T, int dtype, int64_t n, int32_t m, int64_t excl, double p,
+                      double *P, int64_t *I, void *ws, size_t ws_bytes, const mp_options *opt,
+                      int64_t slice_cells, int force, mp_options *best, double *times_ms,
+                      int32_t max_times, int32_t *n_times, void *stream) {
+    g_err[0] = 0;
+    if (!best) return fail(MP_ERR_INVALID_ARG, "best is NULL");
+    if (n_times) *n_times = 0;
+    Problem pb{};
+    pb.dist = dist;
+    pb.dtype = dtype;
+    pb.n = n;
+    pb.m = m;
+    pb.excl = excl;
+    pb.p = dist == MP_DIST_PNORM ? p : 2.0;
+    if (dist < MP_DIST_EUCLID || dist > MP_DIST_ZNORM) return fail(MP_ERR_INVALID_ARG, "dist %d", dist);
+    mp_status s = check_problem(pb, T, P, I, opt);
+    if (s != MP_OK) return s;
+    *best = pb.opt;
+    // candidates: (variant, reanchor)
+    struct Cand { int variant, reanchor; };
+    Cand cands[8];
+    int nc = 0;
+    if (pb.dist != MP_DIST_ZNORM && pb.opt.precision == MP_PREC_FP32) {
+        Problem q = pb;
+        q.opt.reanchor = 0;
+        if (fast_path_applies(q)) {
+            if (kind_of(pb.dist, pb.p) == mpk::K_P2) cands[nc++] = {MP_VARIANT_FAST_FILTER, 0};
+            cands[nc++] = {MP_VARIANT_FAST, 0};
+        }
+        // the generic kernel with its default interval and with 16, 32, 64 rows,
+        // each effective interval (choose_block) once
+        int seen[4], ns = 0;
+        for (int target : {0, 16, 32, 64}) {
+            int B = 0, Q = 0;
+            choose_block(m, target, mpk::SW_QMAX, B, Q);
+            bool dup = false;
+            for (int t = 0; t < ns; ++t) dup |= seen[t] == B;
+            if (dup || (target > 0 && B != target)) continue;
+            seen[ns++] = B;
+            cands[nc++] = {MP_VARIANT_GENERIC, target};
+        }
+    }
+    if (nc <= 1) {  // nothing to choose
+        if (nc == 1) {
+            best->variant = cands[0].variant;
+            best->reanchor = cands[0].reanchor;
+        }
+        return MP_OK;
+    }
+    const std::string key = tune_key(dist, dtype, m, pb.N, pb.p);
+    if (!force) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            best->variant = it->second.variant;
+            best->reanchor = it->second.reanchor;
+            return MP_OK;
+        }
+    }
+    // the whole diagonal range by default: on a slice the profile's thresholds
+    // stay as loose as at the start of a sweep, which misjudges the block filter
+    const long long K = slice_cells > 0 ? std::max<long long>(
+                                              1, std::min<long long>(pb.N - pb.k_first,
+                                                                     slice_cells / std::max<long long>(pb.N, 1)))
+                                        : pb.N - pb.k_first;
+    if (pb.N - pb.k_first <= 0) return MP_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    cudaEvent_t user0 = g_ev_start, user1 = g_ev_end;
+    double bestms = 1e300;
+    int bi = -1;
+    for (int c = 0; c < nc; ++c) {
+        mp_options o = pb.opt;
+        o.variant = cands[c].variant;
+        o.reanchor = cands[c].reanchor;
+        o.polish = 0;
+        o.k_begin = pb.k_first;
+        o.k_end = pb.k_first + K;
+        Problem q = pb;
+        g_ev_start = nullptr;
+        g_ev_end = nullptr;
+        s = run(q, T, P, I, ws, ws_bytes, &o, stream);  // warm-up
+        if (s == MP_OK) {
+            q = pb;
+            g_ev_start = e0;  // the sweep kernel alone
+            g_ev_end = e1;
+            s = run(q, T, P, I, ws, ws_bytes, &o, stream);
+        }
+        g_ev_start = user0;
+        g_ev_end = user1;
+        if (s != MP_OK) break;
+        e = cudaStreamSynchronize(st);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            s = cuda_fail(e, "timing a candidate");
+            break;
+        }
+        if (times_ms && c < max_times) times_ms[c] = ms;
+        if (ms < bestms) {
+            bestms = ms;
+            bi = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != MP_OK) return s;
+    if (n_times) *n_times = nc;
+    best->variant = cands[bi].variant;
+    best->reanchor = cands[bi].reanchor;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = TuneEntry{cands[bi].variant, cands[bi].reanchor, bestms};
+    return MP_OK;
+}
+
+mp_status mp_autotune_cache_save(const char *path) {
+    g_err[0] = 0;
+    if (!path) return fail(MP_ERR_INVALID_ARG, "path is NULL");
+    FILE *f = fopen(path, "w");
+    if (!f) return fail(MP_ERR_INVALID_ARG, "cannot write %s", path);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    fprintf(f, "# mp autotune cache: key variant reanchor ms\n");
+    for (const auto &kv : g_tune)
+        fprintf(f, "%s %d %d %.6f\n", kv.first.c_str(), kv.second.variant, kv.second.reanchor, kv.second.ms);
+    fclose(f);
+    return MP_OK;
+}
+
+mp_status mp_autotune_cache_load(const char *path) {
+    g_err[0] = 0;
+    if (!path) return fail(MP_ERR_INVALID_ARG, "path is NULL");
+    FILE *f = fopen(path, "r");
+    if (!f) return fail(MP_ERR_INVALID_ARG, "cannot read %s", path);
+    std::map<std::string, TuneEntry> add;
+    char line[512];
+    int lineno = 0;
+    while (fgets(line, sizeof line, f)) {
+        ++lineno;
+        if (line[0] == '#' || line[0] == '\n') continue;
+        char key[300];
+        TuneEntry t;
+        if (sscanf(line, "%299s %d %d %lf", key, &t.variant, &t.reanchor, &t.ms) != 4 ||
+            t.variant < MP_VARIANT_AUTO || t.variant > MP_VARIANT_GENERIC || t.reanchor < 0) {
+            fclose(f);
+            return fail(MP_ERR_INVALID_ARG, "%s:%d: malformed entry", path, lineno);
+        }
+        add[key] = t;
+    }
+    fclose(f);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto &kv : add) g_tune[kv.first] = kv.second;
+    return MP_OK;
+}
+
+int64_t mp_autotune_cache_size(void) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    return static_cast<int64_t>(g_tune.size());
 }
 
 }  // extern "C"

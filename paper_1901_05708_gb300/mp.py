@@ -29,6 +29,7 @@ MP_OK, MP_ERR_INVALID_ARG, MP_ERR_UNSUPPORTED, MP_ERR_WORKSPACE, MP_ERR_CUDA, MP
 MP_F32, MP_F64 = 0, 1
 MP_PREC_FP32, MP_PREC_FP64 = 0, 1
 MP_DIST_EUCLID, MP_DIST_PNORM, MP_DIST_ZNORM = 0, 1, 2
+MP_VARIANT_AUTO, MP_VARIANT_FAST_FILTER, MP_VARIANT_FAST, MP_VARIANT_GENERIC = 0, 1, 2, 3
 
 EXPORTS = ("mp_options_default", "mp_workspace_size", "mp_aamp", "mp_pnorm", "mp_acamp",
            "mp_sync_status", "mp_last_error", "mp_status_string", "mp_version", "mp_launch_count",
@@ -37,7 +38,8 @@ EXPORTS = ("mp_options_default", "mp_workspace_size", "mp_aamp", "mp_pnorm", "mp
            "mp_stream_append", "mp_stream_read", "mp_stream_windows", "mp_stream_destroy",
            "mp_anytime_create", "mp_anytime_run", "mp_anytime_read", "mp_anytime_tiles_done",
            "mp_anytime_tiles_total", "mp_anytime_checkpoint_size", "mp_anytime_checkpoint",
-           "mp_anytime_restore", "mp_anytime_destroy")
+           "mp_anytime_restore", "mp_anytime_destroy", "mp_autotune", "mp_autotune_cache_save",
+           "mp_autotune_cache_load", "mp_autotune_cache_size")
 
 
 class MPError(RuntimeError):
@@ -53,7 +55,7 @@ _STATUS = {0: "MP_OK", 1: "MP_ERR_INVALID_ARG", 2: "MP_ERR_UNSUPPORTED", 3: "MP_
 class Options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("precision", ctypes.c_int32),
                 ("reanchor", ctypes.c_int32), ("polish", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("k_begin", ctypes.c_int64),
+                ("variant", ctypes.c_int32), ("k_begin", ctypes.c_int64),
                 ("k_end", ctypes.c_int64)]
 
 
@@ -142,17 +144,27 @@ def load(path: str | None = None):
         lib.mp_anytime_restore.restype = ctypes.c_int
         lib.mp_anytime_destroy.argtypes = [vp]
         lib.mp_anytime_destroy.restype = ctypes.c_int
+        lib.mp_autotune.argtypes = [ctypes.c_int, vp, ctypes.c_int, i64, i32, i64, d, vp, vp, vp, sz, opt_p, i64,
+                                    ctypes.c_int, opt_p, ctypes.POINTER(d), i32, ctypes.POINTER(i32), vp]
+        lib.mp_autotune.restype = ctypes.c_int
+        lib.mp_autotune_cache_save.argtypes = [ctypes.c_char_p]
+        lib.mp_autotune_cache_save.restype = ctypes.c_int
+        lib.mp_autotune_cache_load.argtypes = [ctypes.c_char_p]
+        lib.mp_autotune_cache_load.restype = ctypes.c_int
+        lib.mp_autotune_cache_size.argtypes = []
+        lib.mp_autotune_cache_size.restype = i64
         _lib = lib
         return lib
 
 
 def options(precision: str = "fp32", reanchor: int = 0, polish: bool = True,
-            k_range: tuple[int, int] | None = None) -> Options:
+            k_range: tuple[int, int] | None = None, variant: int = MP_VARIANT_AUTO) -> Options:
     o = Options()
     load().mp_options_default(ctypes.byref(o))
     o.precision = {"fp32": MP_PREC_FP32, "fp64": MP_PREC_FP64}[precision]
     o.reanchor = int(reanchor)
     o.polish = 1 if polish else 0
+    o.variant = int(variant)
     if k_range is not None:
         o.k_begin, o.k_end = int(k_range[0]), int(k_range[1])
     return o
@@ -218,25 +230,25 @@ def _call(fn_name: str, dist: int, T, m: int, excl: int, p: float | None, opt: O
     return P, I
 
 
-def aamp(T, m: int, excl: int, *, precision="fp32", reanchor=0, polish=True, k_range=None,
+def aamp(T, m: int, excl: int, *, precision="fp32", reanchor=0, polish=True, k_range=None, variant=0,
          out=None, stream=None):
     """Matrix profile with the pure Euclidean distance (Algorithm 1)."""
     return _call("mp_aamp", MP_DIST_EUCLID, T, m, excl, None,
-                 options(precision, reanchor, polish, k_range), out, stream)
+                 options(precision, reanchor, polish, k_range, variant), out, stream)
 
 
 def pnorm(T, m: int, excl: int, p: float, *, precision="fp32", reanchor=0, polish=True,
-          k_range=None, out=None, stream=None):
+          k_range=None, variant=0, out=None, stream=None):
     """Matrix profile with the p-norm distance (Algorithm 3)."""
     return _call("mp_pnorm", MP_DIST_PNORM, T, m, excl, p,
-                 options(precision, reanchor, polish, k_range), out, stream)
+                 options(precision, reanchor, polish, k_range, variant), out, stream)
 
 
-def acamp(T, m: int, excl: int, *, precision="fp32", reanchor=0, polish=True, k_range=None,
+def acamp(T, m: int, excl: int, *, precision="fp32", reanchor=0, polish=True, k_range=None, variant=0,
           out=None, stream=None):
     """Matrix profile with the z-normalised Euclidean distance (Algorithm 2)."""
     return _call("mp_acamp", MP_DIST_ZNORM, T, m, excl, None,
-                 options(precision, reanchor, polish, k_range), out, stream)
+                 options(precision, reanchor, polish, k_range, variant), out, stream)
 
 
 def sync_status(stream=None):
@@ -477,3 +489,41 @@ class Anytime:
             self.close()
         except Exception:
             pass
+
+
+def autotune(T, m: int, excl: int, dist="euclid", p: float = 2.0, precision: str = "fp32",
+             slice_cells: int = 0, force: bool = False, stream=None):
+    """Time the kernel variants for this problem (mp_autotune); returns
+    (kwargs for aamp / pnorm / acamp / profile, candidate times in ms)."""
+    lib = load()
+    T, dtype = _prep(T)
+    n = T.numel()
+    N = n - m + 1
+    code = _DIST_CODES.get(dist, dist) if isinstance(dist, str) else int(dist)
+    opt = options(precision)
+    nbytes = max(int(lib.mp_workspace_size(code, dtype, n, m, ctypes.byref(opt))), 256)
+    ws = _workspace(T.device, nbytes)
+    P = torch.empty(max(N, 1), dtype=torch.float64, device=T.device)
+    I = torch.empty(max(N, 1), dtype=torch.int64, device=T.device)
+    best = Options()
+    times = (ctypes.c_double * 8)()
+    nt = ctypes.c_int32()
+    s = stream if stream is not None else torch.cuda.current_stream(T.device)
+    _check(lib.mp_autotune(code, ctypes.c_void_p(T.data_ptr()), dtype, n, m, excl, float(p),
+                           ctypes.c_void_p(P.data_ptr()), ctypes.c_void_p(I.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                           ws.numel(), ctypes.byref(opt), int(slice_cells), 1 if force else 0, ctypes.byref(best),
+                           times, 8, ctypes.byref(nt), ctypes.c_void_p(s.cuda_stream)))
+    return ({"precision": precision, "reanchor": best.reanchor, "variant": best.variant},
+            [times[i] for i in range(nt.value)])
+
+
+def autotune_cache_save(path: str):
+    _check(load().mp_autotune_cache_save(path.encode()))
+
+
+def autotune_cache_load(path: str):
+    _check(load().mp_autotune_cache_load(path.encode()))
+
+
+def autotune_cache_size() -> int:
+    return int(load().mp_autotune_cache_size())

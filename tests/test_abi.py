@@ -160,6 +160,26 @@ def test_stream_checks_need_no_gpu(lib):
     assert lib.mp_stream_destroy(None) == E.MP_OK
 
 
+def test_autotune_cache_files_need_no_gpu(lib, tmp_path):
+    E = mp
+    good = tmp_path / "cache.txt"
+    good.write_text("# comment\nNVIDIA_GB300|0|0|256|20|2 1 0 132.5\nNVIDIA_GB300|1|0|128|18|3 2 0 9.1\n")
+    n0 = lib.mp_autotune_cache_size()
+    assert lib.mp_autotune_cache_load(str(good).encode()) == E.MP_OK
+    assert lib.mp_autotune_cache_size() == n0 + 2
+    out = tmp_path / "out.txt"
+    assert lib.mp_autotune_cache_save(str(out).encode()) == E.MP_OK
+    assert "NVIDIA_GB300|0|0|256|20|2 1 0" in out.read_text()
+    bad = tmp_path / "bad.txt"
+    bad.write_text("key 9 0 1.0\n")
+    assert lib.mp_autotune_cache_load(str(bad).encode()) == E.MP_ERR_INVALID_ARG
+    assert lib.mp_autotune_cache_load(str(tmp_path / "missing.txt").encode()) == E.MP_ERR_INVALID_ARG
+    o = mp.Options()
+    lib.mp_options_default(ctypes.byref(o))
+    o.variant = 7
+    assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG
+
+
 def test_binding_refuses_cpu_tensors(lib):
     torch = pytest.importorskip("torch")
     with pytest.raises(TypeError):
