@@ -407,9 +407,11 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
                 za.tiles = mpk::z_prefix(za.L, za.nb);
                 if (za.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", za.tiles);
                 const size_t smem = mpk::sweepz_smem_bytes();
-                e = cudaFuncSetAttribute(mpk::sweepz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                const bool filter = pb.N >= FILTER_MIN_N;
+                auto kern = filter ? mpk::sweepz_kernel<true> : mpk::sweepz_kernel<false>;
+                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e == cudaSuccess && za.tiles > 0) {
-                    mpk::sweepz_kernel<<<static_cast<unsigned>(za.tiles), mpk::Z_NT, smem, st>>>(za);
+                    kern<<<static_cast<unsigned>(za.tiles), mpk::Z_NT, smem, st>>>(za);
                     e = cudaGetLastError();
                 }
             } else if (pb.dist == MP_DIST_ZNORM) {

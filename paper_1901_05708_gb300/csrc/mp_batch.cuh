@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(Z_NT, 2) sweepz_batch_kernel(const BatchData d
             za.m = sr->m;
         }
         __syncthreads();
-        sweepz_tile(za, tile.band, tile.rt, smem);
+        sweepz_tile<false>(za, tile.band, tile.rt, smem);
         __syncthreads();
     }
 }

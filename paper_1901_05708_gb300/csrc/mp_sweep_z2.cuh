@@ -66,17 +66,23 @@ __device__ __forceinline__ bool z_decode(const SweepZArgs &a, long long t, long 
     return rt >= 0 && rt * Z_S < Lb;
 }
 
+__host__ __device__ inline size_t sweepz_thr_bytes() {
+    const size_t nc = v2_cpos(Z_KW + Z_RC + 16);  // column thresholds, per stream
+    return ((2 * (Z_RC + 8) + 2 * nc) * sizeof(float) + 15) / 16 * 16;
+}
+
 inline size_t sweepz_smem_bytes() {
     const size_t nj = v2_jpos(Z_KW + Z_RC + 16) + 2;  // per j-side array
     const size_t ni = Z_RC + 16;                       // per i-side array
-    const size_t nc = v2_cpos(Z_KW + Z_RC + 16);       // column thresholds, per stream
-    return 3 * (nj + ni) * sizeof(float2) + (2 * (Z_RC + 8) + 2 * nc) * sizeof(float);
+    // + the covariance words saved at the start of a filtered block (8 float4 per thread)
+    return 3 * (nj + ni) * sizeof(float2) + sweepz_thr_bytes() + 8 * Z_NT * sizeof(float4);
 }
 
 __device__ __forceinline__ float2 z_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
 // One tile (band, rt) of one problem; every thread of the CTA calls it (the
 // chunk loop synchronises the whole CTA).
+template <bool FILTER>
 __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band, long long rt,
                                             unsigned char *smem) {
     const int m = a.m;
@@ -99,6 +105,7 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
     const int ncs = v2_cpos(Z_KW + Z_RC + 16);
     float *thr_ca = thr_r + 2 * (Z_RC + 8);
     float *thr_cb = thr_ca + ncs;
+    float4 *zsave = reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(thr_r) + sweepz_thr_bytes());
 
     const int jb = tid * Z_D;
     const long long kt = k0 + jb;
@@ -163,6 +170,7 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
     // done in chunk 0); blocks of 8 rows keep every window 16-byte aligned.
     const int nchunks_cta = Hs > 1 ? (Hs - 1 + Z_RC - 1) / Z_RC : 1;
     int ulast = 0;
+    int skip = 0, backoff = 1;  // filter: blocks to run tracked without a filter pass; next skip length
     for (int c = 0; c < nchunks_cta; ++c) {
         const int u0c = c * Z_RC;
         __syncthreads();  // the previous chunk is done with shared memory
@@ -251,7 +259,29 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
             }
         };
 
-        if (c == 0) masked_row(0, 0, 0);  // the anchor row
+        // Offer the partial minima of the columns still open after stream-local
+        // row ul (slot sl holds column ul + ((sl - ul) mod D)) and close them.
+        auto flush_open = [&](int ul) {
+#pragma unroll
+            for (int sl = 0; sl < Z_D; ++sl) {
+                const int delta = ((sl - ul) % Z_D + Z_D) % Z_D;
+                if (delta != 0) {
+                    const int uc = ul + delta;
+                    const int ci = v2_cpos(jb + uc - u0c);
+                    if (ca[sl] != NONE && ca[sl] <= thr_ca[ci])
+                        v2_emit(a.keys, thr_ca, ci, col_tgt(uc, 0), ca[sl], kt, 0);
+                    if (cb[sl] != NONE && cb[sl] <= thr_cb[ci])
+                        v2_emit(a.keys, thr_cb, ci, col_tgt(uc, 1), cb[sl], kt, 0);
+                }
+                ca[sl] = NONE;
+                cb[sl] = NONE;
+            }
+        };
+
+        if (c == 0) {
+            masked_row(0, 0, 0);  // the anchor row
+            if (FILTER) flush_open(0);  // with the filter, column slots never cross a fast block
+        }
         const float4 *JF4 = reinterpret_cast<const float4 *>(JF);
         const float4 *JG4 = reinterpret_cast<const float4 *>(JG);
         const float4 *JI4 = reinterpret_cast<const float4 *>(JI);
@@ -261,6 +291,7 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
             if (u0c + ulb + Z_D < ufast) {
                 // ---- fast block: rows ufirst .. ufirst + 7, all cells valid
                 float2 WF[2 * Z_D], WG[2 * Z_D], WI[2 * Z_D];
+                bool track = true;
                 const int qb = 5 * ((jb + ulb) >> 3);
 #pragma unroll
                 for (int q = 0; q < Z_D; ++q) {
@@ -275,6 +306,63 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                 }
                 const float *tra = thr_r + ulb, *trb = trb_base + ulb;
                 const float *tca = thr_ca + v2_cpos(jb + ulb), *tcb = thr_cb + v2_cpos(jb + ulb);
+                if (FILTER && skip > 0) {
+                    --skip;
+                } else if (FILTER) {
+                    // ---- filter pass: the covariance steps and one running minimum of the
+                    // block's scores per stream against the loosest threshold of the rows
+                    // and columns they feed; the warp replays the block tracked (from the
+                    // words saved in shared memory) only if some lane could pass
+#pragma unroll
+                    for (int p2 = 0; p2 < Z_D / 2; ++p2) {
+                        zsave[p2 * Z_NT + tid] = make_float4(ch[2 * p2].x, ch[2 * p2].y, ch[2 * p2 + 1].x, ch[2 * p2 + 1].y);
+                        zsave[(p2 + 4) * Z_NT + tid] =
+                            make_float4(cl[2 * p2].x, cl[2 * p2].y, cl[2 * p2 + 1].x, cl[2 * p2 + 1].y);
+                    }
+                    float bma = NONE, bmb = NONE;
+#pragma unroll
+                    for (int ul = 1; ul <= Z_D; ++ul) {
+                        step(ulb + ul, WF, WG, ul);
+#pragma unroll
+                        for (int d = 0; d < Z_D; d += 2) {
+                            const float2 qa = score(II[ulb + ul], WI[ul + d], d);
+                            const float2 qb = score(II[ulb + ul], WI[ul + d + 1], d + 1);
+                            bma = min3f(bma, qa.x, qb.x);
+                            bmb = min3f(bmb, qa.y, qb.y);
+                        }
+                        if ((ul & 1) == 0) renorm();
+                    }
+                    float tma = max3f(tra[1], tra[2], tra[3]), tmb = max3f(trb[1], trb[2], trb[3]);
+                    tma = max3f(tma, tra[4], tra[5]);
+                    tmb = max3f(tmb, trb[4], trb[5]);
+                    tma = max3f(tma, tra[6], tra[7]);
+                    tmb = max3f(tmb, trb[6], trb[7]);
+                    tma = max3f(tma, tra[8], tca[1]);
+                    tmb = max3f(tmb, trb[8], tcb[1]);
+#pragma unroll
+                    for (int x = 2; x < 2 * Z_D; x += 2) {
+                        tma = max3f(tma, tca[x + (x >> 3)], tca[x + 1 + ((x + 1) >> 3)]);
+                        tmb = max3f(tmb, tcb[x + (x >> 3)], tcb[x + 1 + ((x + 1) >> 3)]);
+                    }
+                    // a tagged score is at least the score with its tag bits cleared
+                    track = __any_sync(__activemask(), __int_as_float(__float_as_int(bma) & tag_mask) <= tma ||
+                                                           __int_as_float(__float_as_int(bmb) & tag_mask) <= tmb);
+                    if (__builtin_expect(track, 0)) {
+#pragma unroll
+                        for (int p2 = 0; p2 < Z_D / 2; ++p2) {
+                            const float4 h = zsave[p2 * Z_NT + tid], l = zsave[(p2 + 4) * Z_NT + tid];
+                            ch[2 * p2] = make_float2(h.x, h.y);
+                            ch[2 * p2 + 1] = make_float2(h.z, h.w);
+                            cl[2 * p2] = make_float2(l.x, l.y);
+                            cl[2 * p2 + 1] = make_float2(l.z, l.w);
+                        }
+                        skip = backoff;
+                        backoff = backoff < 32 ? 2 * backoff : 32;
+                    } else {
+                        backoff = 1;
+                    }
+                }
+                if (track) {
 #pragma unroll
                 for (int pr = 0; pr < Z_D / 2; ++pr) {
                     const int ul0 = 2 * pr + 1, ul1 = ul0 + 1;  // block-local rows
@@ -328,6 +416,8 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                     ca[j1] = NONE;
                     cb[j1] = NONE;
                 }
+                if (FILTER) flush_open(u0c + ulb + Z_D);
+                }
                 ulast = u0c + ulb + Z_D;
             } else {
                 // ---- masked rows, one at a time (u % 8 stays a compile-time constant)
@@ -366,6 +456,7 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
     }
 }
 
+template <bool FILTER>
 __global__ void __launch_bounds__(Z_NT, 2) sweepz_kernel(const SweepZArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     long long band, rt;
@@ -373,7 +464,7 @@ __global__ void __launch_bounds__(Z_NT, 2) sweepz_kernel(const SweepZArgs a) {
         if (threadIdx.x == 0) atomicOr(&mp_device_error, ERR_BAD_TILE);
         return;
     }
-    sweepz_tile(a, band, rt, smem);
+    sweepz_tile<FILTER>(a, band, rt, smem);
 }
 
 }  // namespace mpk

@@ -205,6 +205,25 @@ def test_long_walk_filter_kernel(mp):
     assert np.all(I >= 0) and np.all(np.abs(I - x) > s.excl)
 
 
+def test_long_znorm_filter_kernel(mp):
+    """A 250,000-point walk with a flat run (z-normalised, filter kernel): the
+    flat rows get no neighbour and are nobody's neighbour; sampled rows, the
+    flat run's edges included, match brute force."""
+    s = W.small("flat", 250_000, 64, 85, dtype=np.float32)
+    mu, S, flat = oracle.window_stats(s.T, s.m)
+    assert flat.sum() > 0
+    fr = np.nonzero(flat)[0]
+    extra = [fr[0] - 1, fr[0], fr[-1], fr[-1] + 1]
+    rows = np.unique(np.concatenate([np.random.default_rng(4).choice(s.N, 250, replace=False), extra]))
+    rows = rows[(rows >= 0) & (rows < s.N)]
+    ref = oracle.brute_rows(s.T, s.m, s.excl, rows, "znorm")
+    P, I = run(mp, s.T, s.m, s.excl, "znorm")
+    assert np.all(np.isinf(P[flat])) and np.all(I[flat] == -1)
+    assert not np.any(flat[I[I >= 0]])
+    parity.check(s.T, s.m, s.excl, "znorm", 2.0, P, I, RTOL32, rows=rows, P_ref=ref[0], I_ref=ref[1], P2=ref[2],
+                 label="long z")
+
+
 @pytest.mark.parametrize("dist,p", [("euclid", 2.0), ("pnorm", 1.0), ("pnorm", 3.0)])
 def test_fast_and_generic_kernels_agree(mp, monkeypatch, dist, p):
     """Fast and generic FP32 kernels against the oracle on a series with many
