@@ -71,14 +71,19 @@ typedef enum { MP_DIST_EUCLID = 0, MP_DIST_PNORM = 1, MP_DIST_ZNORM = 2 } mp_dis
 /* Kernel of the FP32 Euclidean / p-norm sweep (the z-normalised distance has
  * one FP32 kernel).  AUTO: the two-stream kernel where it applies (FP32
  * input, m a multiple of 32, p in {1, 2, 3}, default re-anchor interval),
- * with the block filter for p = 2 and N >= 200,000; else the generic kernel.
+ * with the block filter for p = 2 and N >= 200,000; else, for m > 1024 and
+ * p in {1, 2, 3} (or where the generic kernel's shared memory does not fit
+ * m), the tall-tile kernel; else the generic kernel.
  * The others force a choice (MP_ERR_UNSUPPORTED where it does not apply);
  * mp_autotune times them. */
 typedef enum {
     MP_VARIANT_AUTO = 0,
     MP_VARIANT_FAST_FILTER = 1,  /* two-stream kernel with the block filter (p = 2) */
     MP_VARIANT_FAST = 2,         /* two-stream kernel                               */
-    MP_VARIANT_GENERIC = 3       /* generic kernel (any m, p, input type; reanchor)  */
+    MP_VARIANT_GENERIC = 3,      /* generic kernel (any p, input type; reanchor;     */
+                                 /* shared memory limits m to about 12,000)          */
+    MP_VARIANT_TALL = 4          /* tall-tile kernel: float-float sums, tiles of      */
+                                 /* max(8192, 8m) rows (p in {1, 2, 3}; long windows) */
 } mp_variant;
 
 typedef struct mp_options {

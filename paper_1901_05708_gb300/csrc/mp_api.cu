@@ -140,7 +140,7 @@ mp_status check_problem(Problem &pb, const void *T, const double *P, const int64
         return fail(MP_ERR_INVALID_ARG, "precision %d", pb.opt.precision);
     if (pb.opt.reanchor < 0) return fail(MP_ERR_INVALID_ARG, "reanchor %d < 0", pb.opt.reanchor);
     if (pb.opt.polish != 0 && pb.opt.polish != 1) return fail(MP_ERR_INVALID_ARG, "polish %d", pb.opt.polish);
-    if (pb.opt.variant < MP_VARIANT_AUTO || pb.opt.variant > MP_VARIANT_GENERIC)
+    if (pb.opt.variant < MP_VARIANT_AUTO || pb.opt.variant > MP_VARIANT_TALL)
         return fail(MP_ERR_INVALID_ARG, "variant %d", pb.opt.variant);
     if (pb.opt.k_begin < 0) return fail(MP_ERR_INVALID_ARG, "k_begin %lld < 0", (long long)pb.opt.k_begin);
     if (!T || !P || !I) return fail(MP_ERR_INVALID_ARG, "NULL T, P or I");
@@ -286,8 +286,65 @@ mp_status run_sweep2(const Problem &pb, const Layout &L, char *ws, cudaStream_t 
     }
 }
 
+template <int KIND, bool FILTER>
+mp_status launch_tall_t(const mpk::SweepZArgs &a, cudaStream_t st) {
+    const size_t smem = mpk::sweepz_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(mpk::sweepz_kernel<KIND, FILTER>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tall sweep)");
+    {
+        SweepEvents ev(st);
+        mpk::sweepz_kernel<KIND, FILTER><<<static_cast<unsigned>(a.tiles), mpk::Z_NT, smem, st>>>(a);
+    }
+    counted();
+    return cudaGetLastError() == cudaSuccess ? MP_OK : cuda_fail(cudaGetLastError(), "tall sweep launch");
+}
+
+// Tall-tile Euclidean / p-norm sweep (float-float sums, tiles of max(8192, 8m) rows).
+mp_status run_tall(const Problem &pb, const Layout &L, char *ws, cudaStream_t st) {
+    mpk::SweepZArgs a{};
+    a.t = reinterpret_cast<const float *>(ws + L.hi);
+    a.keys = reinterpret_cast<unsigned long long *>(ws + L.keys);
+    a.n = pb.n;
+    a.N = pb.N;
+    a.k_first = pb.k_first;
+    a.k_end = pb.k_end;
+    a.m = pb.m;
+    a.L = pb.N - pb.k_first;
+    a.nb = (pb.k_end - pb.k_first + mpk::Z_KW - 1) / mpk::Z_KW;
+    a.S = mpk::z_rows_per_tile(pb.m);
+    a.tiles = mpk::z_prefix(a.L, a.nb, a.S);
+    if (a.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", a.tiles);
+    if (a.tiles <= 0) return MP_OK;
+    switch (kind_of(pb.dist, pb.p)) {
+        case mpk::K_P1: return launch_tall_t<mpk::K_P1, false>(a, st);
+        case mpk::K_P3: return launch_tall_t<mpk::K_P3, false>(a, st);
+        default:
+            return pb.N >= FILTER_MIN_N ? launch_tall_t<mpk::K_P2, true>(a, st) : launch_tall_t<mpk::K_P2, false>(a, st);
+    }
+}
+
+// The generic kernel's shared memory for this problem (0 if it cannot hold m).
+size_t generic_smem(const Problem &pb) {
+    int B = 0, Q = 0;
+    choose_block(pb.m, pb.opt.reanchor, mpk::SW_QMAX, B, Q);
+    const size_t smem = mpk::sweep_smem_bytes(2048, pb.m, Q, pb.dtype == MP_F64);
+    return smem > 227 * 1024 ? 0 : smem;
+}
+
+bool tall_applies(const Problem &pb) {
+    return pb.dist != MP_DIST_ZNORM && kind_of(pb.dist, pb.p) != mpk::K_PG && pb.opt.precision == MP_PREC_FP32;
+}
+
+bool use_tall(const Problem &pb) {
+    if (pb.opt.variant == MP_VARIANT_TALL) return true;
+    if (pb.opt.variant != MP_VARIANT_AUTO || !tall_applies(pb) || getenv_generic()) return false;
+    return generic_smem(pb) == 0 || (pb.m > 1024 && pb.dtype == MP_F32);
+}
+
 mp_status run_sweep_f32(const Problem &pb, const Layout &L, char *ws, cudaStream_t st) {
     if (fast_path_ok(pb)) return run_sweep2(pb, L, ws, st);
+    if (use_tall(pb)) return run_tall(pb, L, ws, st);
     mpk::SweepArgs a{};
     a.hi = reinterpret_cast<const float *>(ws + L.hi);
     a.lo = L.lo ? reinterpret_cast<const float *>(ws + L.lo) : nullptr;
@@ -336,6 +393,8 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
         return fail(MP_ERR_UNSUPPORTED, "the block filter exists for p = 2 only");
     if (v == MP_VARIANT_GENERIC && (pb.opt.precision != MP_PREC_FP32 || pb.dist == MP_DIST_ZNORM))
         return fail(MP_ERR_UNSUPPORTED, "the generic kernel is the FP32 Euclidean / p-norm sweep");
+    if (v == MP_VARIANT_TALL && !tall_applies(pb))
+        return fail(MP_ERR_UNSUPPORTED, "the tall-tile kernel is the FP32 sweep for p in {1, 2, 3}");
     const Layout L = layout(pb);
     if (!ws) return fail(MP_ERR_WORKSPACE, "workspace is NULL (need %zu bytes)", L.total);
     if (!aligned(ws, ALIGN)) return fail(MP_ERR_INVALID_ARG, "workspace not 256-byte aligned");
@@ -404,11 +463,12 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
                 za.m = pb.m;
                 za.L = pb.N - pb.k_first;
                 za.nb = (pb.k_end - pb.k_first + mpk::Z_KW - 1) / mpk::Z_KW;
-                za.tiles = mpk::z_prefix(za.L, za.nb);
+                za.S = mpk::z_rows_per_tile(pb.m);
+                za.tiles = mpk::z_prefix(za.L, za.nb, za.S);
                 if (za.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", za.tiles);
                 const size_t smem = mpk::sweepz_smem_bytes();
                 const bool filter = pb.N >= FILTER_MIN_N;
-                auto kern = filter ? mpk::sweepz_kernel<true> : mpk::sweepz_kernel<false>;
+                auto kern = filter ? mpk::sweepz_kernel<mpk::K_Z, true> : mpk::sweepz_kernel<mpk::K_Z, false>;
                 e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e == cudaSuccess && za.tiles > 0) {
                     kern<<<static_cast<unsigned>(za.tiles), mpk::Z_NT, smem, st>>>(za);
@@ -908,7 +968,7 @@ static mp_status batch_plan_build(const mp_batch_desc *desc, const mp_options *o
             b.z_off = pl->zwindows;
             pl->zwindows += b.N;
             qi = mp_batch_plan::Q_Z;
-            batch_tiles(q[qi], si, L, mpk::Z_KW, mpk::Z_S);
+            batch_tiles(q[qi], si, L, mpk::Z_KW, static_cast<int>(mpk::z_rows_per_tile(b.m)));
         } else if (b.m % 32 == 0 && mpk::sweep2_smem_bytes(b.m, mpk::V2_QMAX) <= mpk::V2_SMEM_MAX &&
                    (p2 || pl->genp_kind == mpk::K_P1 || pl->genp_kind == mpk::K_P3)) {
             qi = p2 ? mp_batch_plan::Q_FAST2 : mp_batch_plan::Q_FASTP;

@@ -12,7 +12,7 @@ namespace mpk {
 
 // Term of the distance carried by the Euclidean / p-norm sweeps:
 // e^2 (p = 2, Lemma 1), |e| (p = 1), |e|^3 (p = 3), |e|^p (other real p; Lemma 2).
-enum Kind { K_P2 = 0, K_P1 = 1, K_P3 = 2, K_PG = 3 };
+enum Kind { K_P2 = 0, K_P1 = 1, K_P3 = 2, K_PG = 3, K_Z = 4 };  // K_Z: the z-normalised sweep
 
 // Error bits written to the device error word (read back by mp_sync_status).
 enum : int {

@@ -27,6 +27,14 @@
 //    minima.  The winner's slot is read back from the tag, so a candidate
 //    that passes its threshold costs two atomics and nothing else.
 //
+//  * Block filter (FILTER, for p = 2 on long series).  Each 8-row block first
+//    runs the recurrence with one running minimum per stream; unless some
+//    lane of the warp could beat the loosest threshold of the rows and
+//    columns its block feeds, the block is done without tags or slots.
+//    Otherwise the block is replayed from the saved state with the tracked
+//    bookkeeping above, and the next blocks skip the filter for a number of
+//    blocks that doubles while it keeps failing.
+//
 //  * Shared memory holds, per tile, the j-side series as float2 pairs
 //    (stream a, stream b) padded by 16 bytes every 64 so that each lane's
 //    16-byte loads hit distinct banks, the i-side pairs, float thresholds

@@ -20,7 +20,16 @@
 // i side: df, dg, inv of the rows) and the current best values of its rows
 // and columns are staged in shared memory, and the chunk's threads read them
 // with conflict-free 16-byte loads.  Minima are tagged exactly as in the
-// Euclidean fast path.
+// Euclidean fast path, and long series take the same block filter (the
+// covariance words of a filtered block are saved in shared memory for the
+// tracked replay).
+//
+// The same tall, chunked tiles also carry the Euclidean / p-norm sums for
+// long windows (MODE = K_P2, K_P1, K_P3), where the other kernels would pay an
+// O(m) anchor per 2048-row tile: the state is then the float-float sum of the
+// Lemma 1 / 2 terms, the staged operands are the entering and leaving samples
+// t_{w+m-1} and t_{w-1} of each window w, and a tile has S = max(8192, 8m)
+// rows, so the O(m) anchor costs a fixed fraction of the tile.
 #pragma once
 
 #include <cstdint>
@@ -34,9 +43,15 @@ namespace mpk {
 constexpr int Z_NT = 128;             // threads per CTA
 constexpr int Z_D = 8;                // diagonals per thread
 constexpr int Z_KW = Z_NT * Z_D;      // diagonals per band
-constexpr int Z_HS = 4096;            // rows per stream per tile (at most)
-constexpr int Z_S = 2 * Z_HS;         // rows per tile
+constexpr int Z_S = 8192;             // rows per tile (at least; S = max(Z_S, 8m) rounded to 2 RC)
 constexpr int Z_RC = 256;             // rows per stream per chunk
+
+// rows per tile for window length m
+__host__ __device__ inline long long z_rows_per_tile(long long m) {
+    long long S = 8 * m;
+    S = (S + 2 * Z_RC - 1) / (2 * Z_RC) * (2 * Z_RC);
+    return S < Z_S ? Z_S : S;
+}
 
 struct SweepZArgs {
     const float *t;                   // FP32 series (shifted like the means)
@@ -45,25 +60,27 @@ struct SweepZArgs {
     const float *df, *dg, *inv;       // operands (inv = NaN for a flat window)
     unsigned long long *keys;
     long long n, N, k_first, k_end, L, nb, tiles;
+    long long S;                      // rows per tile (z_rows_per_tile(m))
     int m;
+    float p;                          // exponent of the p-norm modes (unused for K_P1 / K_P2 / K_P3's own term)
 };
 
-__host__ __device__ inline long long z_prefix(long long L, long long b) {
+__host__ __device__ inline long long z_prefix(long long L, long long b, long long S) {
     if (b <= 0) return 0;
-    return floor_sum(b, Z_S, Z_KW, L + Z_S - 1 - (b - 1) * Z_KW);
+    return floor_sum(b, S, Z_KW, L + S - 1 - (b - 1) * Z_KW);
 }
 
 __device__ __forceinline__ bool z_decode(const SweepZArgs &a, long long t, long long &band, long long &rt) {
     long long lo = 0, hi = a.nb - 1;
     while (lo < hi) {
         const long long mid = (lo + hi + 1) / 2;
-        if (z_prefix(a.L, mid) <= t) lo = mid;
+        if (z_prefix(a.L, mid, a.S) <= t) lo = mid;
         else hi = mid - 1;
     }
     band = lo;
-    rt = t - z_prefix(a.L, lo);
+    rt = t - z_prefix(a.L, lo, a.S);
     const long long Lb = a.L - lo * Z_KW;
-    return rt >= 0 && rt * Z_S < Lb;
+    return rt >= 0 && rt * a.S < Lb;
 }
 
 __host__ __device__ inline size_t sweepz_thr_bytes() {
@@ -82,15 +99,27 @@ __device__ __forceinline__ float2 z_mul(float2 a, float2 b) { return __fmul2_rn(
 
 // One tile (band, rt) of one problem; every thread of the CTA calls it (the
 // chunk loop synchronises the whole CTA).
-template <bool FILTER>
+// term of the p-norm modes for both streams: x^2, |x|, |x|^3
+template <int MODE>
+__device__ __forceinline__ float2 z_term(float2 x) {
+    if constexpr (MODE == K_P1) return make_float2(fabsf(x.x), fabsf(x.y));
+    else if constexpr (MODE == K_P3) {
+        const float2 x2 = __fmul2_rn(x, x);
+        return make_float2(fabsf(x.x) * x2.x, fabsf(x.y) * x2.y);
+    } else return __fmul2_rn(x, x);
+}
+
+template <int MODE, bool FILTER>
 __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band, long long rt,
                                             unsigned char *smem) {
+    constexpr bool ZN = MODE == K_Z;
     const int m = a.m;
     const int tid = threadIdx.x;
+    const long long S = a.S;
     const long long k0 = a.k_first + band * Z_KW;
-    const long long r0 = rt * Z_S;
+    const long long r0 = rt * S;
     const long long Lb = a.L - band * Z_KW;
-    const int Rt = static_cast<int>(Lb - r0 < Z_S ? Lb - r0 : Z_S);
+    const int Rt = static_cast<int>(Lb - r0 < S ? Lb - r0 : S);
     const int Hs = ((Rt + 1) / 2 + Z_D - 1) & ~(Z_D - 1);  // rows per stream, a multiple of 8
     const long long rb = r0 + Hs;                           // first row of stream b
 
@@ -113,7 +142,8 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
     const int nd = nd_ll <= 0 ? 0 : (nd_ll >= Z_D ? Z_D : static_cast<int>(nd_ll));
     const long long lim_ll = a.N - kt - r0;  // tile-local row x of slot d valid iff x + d < lim
     const bool active = nd > 0 && lim_ll > 0;
-    const int lim = static_cast<int>(lim_ll <= 0 ? 0 : (lim_ll < 4 * Z_HS ? lim_ll : 4 * Z_HS));
+    const long long lim_cap = 2 * S + 16;
+    const int lim = static_cast<int>(lim_ll <= 0 ? 0 : (lim_ll < lim_cap ? lim_ll : lim_cap));
     const int lim_b = lim - Hs;
     const int steps = lim < Hs ? lim : Hs;  // stream-local rows this thread walks
     int ufast = nd == Z_D ? lim_b - (Z_D - 1) : 0;
@@ -123,9 +153,31 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
     const int tag_mask = ~(Z_D - 1);
     const float2 ONE = make_float2(1.f, 1.f);
 
-    // ---- anchors: cov of (row r_s, diagonal kt + d) in float-float, from the definition
-    float2 ch[Z_D], cl[Z_D];  // negated covariance, hi and lo
-    if (active) {
+    // ---- anchors in float-float, from the definition: the covariance of (row r_s,
+    // diagonal kt + d) (z-norm, stored negated), or the sum of the p-norm terms
+    float2 ch[Z_D], cl[Z_D];
+    if (active && !ZN) {
+        auto tv = [&](long long g) -> float { return (g >= 0 && g < a.n) ? __ldg(a.t + g) : 0.f; };
+#pragma unroll
+        for (int d = 0; d < Z_D; ++d) {
+            ch[d] = make_float2(0.f, 0.f);
+            cl[d] = make_float2(0.f, 0.f);
+        }
+        for (int l = 0; l < m; ++l) {
+            const float2 ti = make_float2(tv(r0 + l), tv(rb + l));
+#pragma unroll
+            for (int d = 0; d < Z_D; ++d) {
+                const float2 tj = make_float2(tv(r0 + kt + d + l), tv(rb + kt + d + l));
+                const float2 p = z_term<MODE>(v2_sub(ti, tj));
+                const float2 t = add2(ch[d], p);  // TwoSum(ch, p): exact whichever is larger
+                const float2 bb = v2_sub(t, ch[d]);
+                const float2 err = add2(v2_sub(ch[d], v2_sub(t, bb)), v2_sub(p, bb));
+                cl[d] = add2(cl[d], err);
+                ch[d] = t;
+            }
+        }
+    }
+    if (active && ZN) {
         auto tv = [&](long long g) -> float { return (g >= 0 && g < a.n) ? __ldg(a.t + g) : 0.f; };
         auto tl = [&](long long g) -> float { return (a.tlo && g >= 0 && g < a.n) ? __ldg(a.tlo + g) : 0.f; };
         auto mv = [&](const float *p, long long g) -> float { return (g >= 0 && g < a.N) ? __ldg(p + g) : 0.f; };
@@ -160,10 +212,15 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
 #pragma unroll
     for (int d = 0; d < Z_D; ++d) { ca[d] = NONE; cb[d] = NONE; }
 
-    // score of the current state: q = 1 - cov inv_i inv_j (cov = -(ch + cl))
+    // score of the current state: q = 1 - cov inv_i inv_j (cov = -(ch + cl)), or
+    // the p-norm sum ch + cl
     auto score = [&](float2 iI, float2 jI, int d) {
-        const float2 w = z_mul(iI, jI);
-        return fma2(cl[d], w, fma2(ch[d], w, ONE));
+        if constexpr (ZN) {
+            const float2 w = z_mul(iI, jI);
+            return fma2(cl[d], w, fma2(ch[d], w, ONE));
+        } else {
+            return add2(ch[d], cl[d]);
+        }
     };
 
     // Chunk c covers stream-local rows u0c + 1 .. u0c + RC (row 0, the anchor, is
@@ -178,18 +235,33 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
             // j side: element x = partner index (j - 1) - y, y = r_s + u0c + k0 - 1
             const long long ya = r0 + u0c + k0 - 1, yb = ya + Hs;
             auto gv = [&](const float *p, long long g) -> float { return (g >= 0 && g < a.N) ? p[g] : 0.f; };
-            for (int x = tid; x < Z_KW + Z_RC + 16; x += Z_NT) {
-                const int px = v2_jpos(x);
-                JF[px] = make_float2(gv(a.df, ya + x), gv(a.df, yb + x));
-                JG[px] = make_float2(gv(a.dg, ya + x), gv(a.dg, yb + x));
-                JI[px] = make_float2(gv(a.inv, ya + x + 1), gv(a.inv, yb + x + 1));
-            }
-            // i side: chunk row ul uses df, dg of window i - 1 and inv of window i
             const long long ia = r0 + u0c, ib = rb + u0c;
-            for (int ul = tid; ul < Z_RC + 16; ul += Z_NT) {
-                IF[ul] = make_float2(gv(a.df, ia + ul - 1), gv(a.df, ib + ul - 1));
-                IG[ul] = make_float2(gv(a.dg, ia + ul - 1), gv(a.dg, ib + ul - 1));
-                II[ul] = make_float2(gv(a.inv, ia + ul), gv(a.inv, ib + ul));
+            if constexpr (ZN) {
+                for (int x = tid; x < Z_KW + Z_RC + 16; x += Z_NT) {
+                    const int px = v2_jpos(x);
+                    JF[px] = make_float2(gv(a.df, ya + x), gv(a.df, yb + x));
+                    JG[px] = make_float2(gv(a.dg, ya + x), gv(a.dg, yb + x));
+                    JI[px] = make_float2(gv(a.inv, ya + x + 1), gv(a.inv, yb + x + 1));
+                }
+                // i side: chunk row ul uses df, dg of window i - 1 and inv of window i
+                for (int ul = tid; ul < Z_RC + 16; ul += Z_NT) {
+                    IF[ul] = make_float2(gv(a.df, ia + ul - 1), gv(a.df, ib + ul - 1));
+                    IG[ul] = make_float2(gv(a.dg, ia + ul - 1), gv(a.dg, ib + ul - 1));
+                    II[ul] = make_float2(gv(a.inv, ia + ul), gv(a.inv, ib + ul));
+                }
+            } else {
+                // entering and leaving samples of window w = ya + x + 1 (j side) and
+                // w = ia + ul (i side): t_{w+m-1} and t_{w-1}
+                auto sv = [&](long long g) -> float { return (g >= 0 && g < a.n) ? a.t[g] : 0.f; };
+                for (int x = tid; x < Z_KW + Z_RC + 16; x += Z_NT) {
+                    const int px = v2_jpos(x);
+                    JF[px] = make_float2(sv(ya + x + m), sv(yb + x + m));
+                    JG[px] = make_float2(sv(ya + x), sv(yb + x));
+                }
+                for (int ul = tid; ul < Z_RC + 16; ul += Z_NT) {
+                    IF[ul] = make_float2(sv(ia + ul + m - 1), sv(ib + ul + m - 1));
+                    IG[ul] = make_float2(sv(ia + ul - 1), sv(ib + ul - 1));
+                }
             }
             // A target without a candidate yet gets the largest finite threshold, not
             // +inf: a slot that saw only flat windows (NaN scores) holds +inf and
@@ -219,7 +291,7 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
             float ta = NONE, tb = NONE;
 #pragma unroll
             for (int d = 0; d < Z_D; ++d) {
-                const float2 q = score(II[ul], JI[v2_jpos(jb + d + ul)], d);
+                const float2 q = ZN ? score(II[ul], JI[v2_jpos(jb + d + ul)], d) : score(ONE, ONE, d);
                 const float va = (d < nd && u + d < lim) ? v2_tag(q.x, d) : NONE;
                 const float vb = (d < nd && u + d < lim_b) ? v2_tag(q.y, d) : NONE;
                 ta = fminf(ta, va);
@@ -246,8 +318,17 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
             const float2 fi = IF[ul], gi = IG[ul];
 #pragma unroll
             for (int d = 0; d < Z_D; ++d) {
-                const float2 inc = fma2(fi, WG[o + d], z_mul(WF[o + d], gi));  // df_i dg_j + df_j dg_i
-                cl[d] = v2_sub(cl[d], inc);
+                if constexpr (ZN) {
+                    const float2 inc = fma2(fi, WG[o + d], z_mul(WF[o + d], gi));  // df_i dg_j + df_j dg_i
+                    cl[d] = v2_sub(cl[d], inc);
+                } else {  // + term(e) - term(f), e = t_{i+m-1} - t_{j+m-1}, f = t_{i-1} - t_{j-1}
+                    const float2 e = v2_sub(fi, WF[o + d]), f = v2_sub(gi, WG[o + d]);
+                    if constexpr (MODE == K_P2) {
+                        cl[d] = fma2(e, e, v2_sub(cl[d], z_mul(f, f)));
+                    } else {
+                        cl[d] = add2(cl[d], v2_sub(z_term<MODE>(e), z_term<MODE>(f)));
+                    }
+                }
             }
         };
         auto renorm = [&]() {
@@ -296,7 +377,8 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
 #pragma unroll
                 for (int q = 0; q < Z_D; ++q) {
                     const int o = qb + q + (q >= 4 ? 1 : 0);
-                    const float4 f4 = JF4[o], g4 = JG4[o], i4 = JI4[o];
+                    const float4 f4 = JF4[o], g4 = JG4[o];
+                    const float4 i4 = ZN ? JI4[o] : make_float4(1.f, 1.f, 1.f, 1.f);
                     WF[2 * q] = make_float2(f4.x, f4.y);
                     WF[2 * q + 1] = make_float2(f4.z, f4.w);
                     WG[2 * q] = make_float2(g4.x, g4.y);
@@ -325,8 +407,9 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                         step(ulb + ul, WF, WG, ul);
 #pragma unroll
                         for (int d = 0; d < Z_D; d += 2) {
-                            const float2 qa = score(II[ulb + ul], WI[ul + d], d);
-                            const float2 qb = score(II[ulb + ul], WI[ul + d + 1], d + 1);
+                            const float2 iI = ZN ? II[ulb + ul] : ONE;
+                            const float2 qa = score(iI, WI[ul + d], d);
+                            const float2 qb = score(iI, WI[ul + d + 1], d + 1);
                             bma = min3f(bma, qa.x, qb.x);
                             bmb = min3f(bmb, qa.y, qb.y);
                         }
@@ -371,12 +454,12 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                     float2 q[Z_D];
                     step(ulb + ul0, WF, WG, ul0);
 #pragma unroll
-                    for (int d = 0; d < Z_D; ++d) q[d] = score(II[ulb + ul0], WI[ul0 + d], d);
+                    for (int d = 0; d < Z_D; ++d) q[d] = score(ZN ? II[ulb + ul0] : ONE, WI[ul0 + d], d);
                     v2_tag8(t0a, q, false, tag_mask);
                     v2_tag8(t0b, q, true, tag_mask);
                     step(ulb + ul1, WF, WG, ul1);
 #pragma unroll
-                    for (int d = 0; d < Z_D; ++d) q[d] = score(II[ulb + ul1], WI[ul1 + d], d);
+                    for (int d = 0; d < Z_D; ++d) q[d] = score(ZN ? II[ulb + ul1] : ONE, WI[ul1 + d], d);
                     renorm();
                     v2_tag8(t1a, q, false, tag_mask);
                     v2_tag8(t1b, q, true, tag_mask);
@@ -456,7 +539,7 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
     }
 }
 
-template <bool FILTER>
+template <int MODE, bool FILTER>
 __global__ void __launch_bounds__(Z_NT, 2) sweepz_kernel(const SweepZArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     long long band, rt;
@@ -464,7 +547,7 @@ __global__ void __launch_bounds__(Z_NT, 2) sweepz_kernel(const SweepZArgs a) {
         if (threadIdx.x == 0) atomicOr(&mp_device_error, ERR_BAD_TILE);
         return;
     }
-    sweepz_tile<FILTER>(a, band, rt, smem);
+    sweepz_tile<MODE, FILTER>(a, band, rt, smem);
 }
 
 }  // namespace mpk
