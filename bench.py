@@ -190,6 +190,12 @@ WORKLOADS = {
     "aamp_small": (lambda seed, n: W.aamp_small(seed=seed - 1),
                    "AAMP pure Euclidean, float64 random walk, n = 10,000", 4),
 }
+# the paper's timing data (Sec. 5.1): i.i.d. uniform series, n = 2^18, m from 2^8 to 2^16
+for _lg in (8, 10, 12, 14, 16):
+    WORKLOADS[f"uniform_m{1 << _lg}"] = (
+        (lambda lg: lambda seed, n: W.Series(f"uniform_n262144_m{1 << lg}", W.uniform(1 << 18, seed + 4), 1 << lg,
+                                             W.excl_zone(1 << lg), W.EUCLID))(_lg),
+        f"AAMP pure Euclidean, i.i.d. uniform values, n = 2^18, m = 2^{_lg}", 4)
 
 
 def workload_config(series: W.Series, desc: str = WORKLOADS["aamp_1m"][1], precision: str = "fp32") -> dict:

@@ -339,7 +339,7 @@ bool tall_applies(const Problem &pb) {
 bool use_tall(const Problem &pb) {
     if (pb.opt.variant == MP_VARIANT_TALL) return true;
     if (pb.opt.variant != MP_VARIANT_AUTO || !tall_applies(pb) || getenv_generic()) return false;
-    return generic_smem(pb) == 0 || (pb.m > 1024 && pb.dtype == MP_F32);
+    return generic_smem(pb) == 0 || (pb.m >= 512 && pb.dtype == MP_F32);
 }
 
 mp_status run_sweep_f32(const Problem &pb, const Layout &L, char *ws, cudaStream_t st) {
@@ -1604,7 +1604,7 @@ mp_status mp_autotune(int dist, const void *T, int dtype, int64_t n, int32_t m, 
     *best = pb.opt;
     // candidates: (variant, reanchor)
     struct Cand { int variant, reanchor; };
-    Cand cands[8];
+    Cand cands[10];
     int nc = 0;
     if (pb.dist != MP_DIST_ZNORM && pb.opt.precision == MP_PREC_FP32) {
         Problem q = pb;
@@ -1623,8 +1623,11 @@ mp_status mp_autotune(int dist, const void *T, int dtype, int64_t n, int32_t m, 
             for (int t = 0; t < ns; ++t) dup |= seen[t] == B;
             if (dup || (target > 0 && B != target)) continue;
             seen[ns++] = B;
-            cands[nc++] = {MP_VARIANT_GENERIC, target};
+            Problem g = pb;
+            g.opt.reanchor = target;
+            if (generic_smem(g) > 0) cands[nc++] = {MP_VARIANT_GENERIC, target};
         }
+        if (tall_applies(pb)) cands[nc++] = {MP_VARIANT_TALL, 0};
     }
     if (nc <= 1) {  // nothing to choose
         if (nc == 1) {
@@ -1732,7 +1735,7 @@ mp_status mp_autotune_cache_load(const char *path) {
         char key[300];
         TuneEntry t;
         if (sscanf(line, "%299s %d %d %lf", key, &t.variant, &t.reanchor, &t.ms) != 4 ||
-            t.variant < MP_VARIANT_AUTO || t.variant > MP_VARIANT_GENERIC || t.reanchor < 0) {
+            t.variant < MP_VARIANT_AUTO || t.variant > MP_VARIANT_TALL || t.reanchor < 0) {
             fclose(f);
             return fail(MP_ERR_INVALID_ARG, "%s:%d: malformed entry", path, lineno);
         }

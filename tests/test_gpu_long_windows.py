@@ -1,5 +1,5 @@
 """Long windows: the tall-tile kernel (float-float sums, tiles of max(8192, 8m)
-rows) serves the Euclidean and p-norm sweeps for m > 1024, including window
+rows) serves the Euclidean and p-norm sweeps for m >= 512, including window
 lengths the generic kernel's shared memory cannot hold.  Checked against
 brute-force rows of the FP64 oracle and against the generic kernel where both
 apply."""
