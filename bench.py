@@ -37,6 +37,10 @@ METRIC = "distance-matrix cells/s (GCells/s) at 1 GB300 + % FP32 roofline, FP32 
 UNIT = "GCells/s"
 FP32_INSTR_PER_CELL = 4          # minimum FP32-pipe instructions per cell (Lemma 1 update)
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of one sweep launch, from a one-pass ncu capture of the
+# current kernel on the full-size workload (profiles/aamp_n1048576_m256_launches.md);
+# None where no capture of the current kernel exists.
+SWEEP_DRAM_BYTES = {("aamp_1m", 1 << 20): 12_809_216 + 55_040}
 
 
 def peaks():
@@ -452,11 +456,15 @@ def main():
     peak_cells = sms * FP32_LANES_PER_SM * f_max / instr_per_cell / 1e9
     sweep_avg_ms = float(np.mean(sweep_ms))
     achieved = cells / (sweep_avg_ms * 1e-3) / 1e9
+    traffic = None if args.k_range else SWEEP_DRAM_BYTES.get((args.workload, args.n))
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_cells, "unit": UNIT,
-            "frac": achieved / peak_cells, "traffic": None,
+            "frac": achieved / peak_cells, "traffic": traffic,
             "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {f_max/1e6:.0f} MHz "
                            f"({src} sm_max_mhz) / {instr_per_cell} FP32 instructions per cell",
             "kernel": "diagonal sweep (a3-a5)", "kernel_ms": sweep_avg_ms}
+    if traffic is not None:
+        roof["traffic_note"] = ("bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum); "
+                                "algorithmic: the series and the keys once, ~12.6 MB")
     if clk.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (sms * FP32_LANES_PER_SM * clk["sm_mhz"] * 1e6
                                                      / instr_per_cell / 1e9)
