@@ -100,19 +100,38 @@ __global__ void __launch_bounds__(PREP_NT) fill_u64_kernel(unsigned long long *_
 // thread per window; neighbouring threads read overlapping windows through
 // the cache.  O(n m) FP64 work, a small share of the sweep for m <= 512.
 // One window (X = double, or float for an FP32 series read directly).
+// Sums over a window are taken as four interleaved partial sums (independent
+// FP64 chains and loads in flight), combined pairwise.
 template <typename X>
 __device__ __forceinline__ void window_stats_at(const X *__restrict__ x, long long i, int m, double &mean,
                                                 double &S, unsigned char &flat) {
-    double a = 0.0;
-    for (int l = 0; l < m; ++l) a += static_cast<double>(x[i + l]);
-    mean = a / m;
-    double q = 0.0, r = 0.0;
-    for (int l = 0; l < m; ++l) {
-        const double v = static_cast<double>(x[i + l]);
-        const double d = v - mean;
-        q = fma(d, d, q);
-        r = fma(v, v, r);
+    const X *w = x + i;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int l = 0;
+    for (; l + 4 <= m; l += 4) {
+        a0 += static_cast<double>(w[l]);
+        a1 += static_cast<double>(w[l + 1]);
+        a2 += static_cast<double>(w[l + 2]);
+        a3 += static_cast<double>(w[l + 3]);
     }
+    for (; l < m; ++l) a0 += static_cast<double>(w[l]);
+    mean = ((a0 + a1) + (a2 + a3)) / m;
+    double q0 = 0.0, q1 = 0.0, r0 = 0.0, r1 = 0.0;
+    l = 0;
+    for (; l + 2 <= m; l += 2) {
+        const double v0 = static_cast<double>(w[l]), v1 = static_cast<double>(w[l + 1]);
+        const double d0 = v0 - mean, d1 = v1 - mean;
+        q0 = fma(d0, d0, q0);
+        q1 = fma(d1, d1, q1);
+        r0 = fma(v0, v0, r0);
+        r1 = fma(v1, v1, r1);
+    }
+    if (l < m) {
+        const double v = static_cast<double>(w[l]), d = v - mean;
+        q0 = fma(d, d, q0);
+        r0 = fma(v, v, r0);
+    }
+    const double q = q0 + q1, r = r0 + r1;
     S = q;
     flat = q <= 0x1p-40 * r;
 }
@@ -197,35 +216,63 @@ struct FinalizeArgsT {
 };
 using FinalizeArgs = FinalizeArgsT<double>;
 
+// |v|^p; the products are rounded one by one (no contraction into the caller's
+// sum), so every kernel that polishes gets the same bits.
 __device__ __forceinline__ double pow_abs(double v, double p) {
     v = fabs(v);
     if (p == 1.0) return v;
-    if (p == 2.0) return v * v;
-    if (p == 3.0) return v * v * v;
+    if (p == 2.0) return __dmul_rn(v, v);
+    if (p == 3.0) return __dmul_rn(__dmul_rn(v, v), v);
     return pow(v, p);
 }
 
-// d(i, j) from the definitions (Sec. 2) in FP64.
+// d(i, j) from the definitions (Sec. 2) in FP64, as four interleaved partial
+// sums combined pairwise (independent chains keep loads in flight).
 template <typename X>
 __device__ double exact_score(const FinalizeArgsT<X> &a, long long i, long long j) {
     const X *xi = a.x + i, *xj = a.x + j;
-    double acc = 0.0;
+    const int m = a.m;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     if (a.dist == FIN_EUCLID) {
-        for (int l = 0; l < a.m; ++l) {
+        int l = 0;
+        for (; l + 4 <= m; l += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double d = static_cast<double>(xi[l + u]) - static_cast<double>(xj[l + u]);
+                acc[u] = fma(d, d, acc[u]);
+            }
+        }
+        for (; l < m; ++l) {
             const double d = static_cast<double>(xi[l]) - static_cast<double>(xj[l]);
-            acc = fma(d, d, acc);
+            acc[0] = fma(d, d, acc[0]);
         }
     } else if (a.dist == FIN_PNORM) {
-        for (int l = 0; l < a.m; ++l) acc += pow_abs(static_cast<double>(xi[l]) - static_cast<double>(xj[l]), a.p);
+        int l = 0;
+        for (; l + 4 <= m; l += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                acc[u] = __dadd_rn(acc[u], pow_abs(static_cast<double>(xi[l + u]) - static_cast<double>(xj[l + u]), a.p));
+        }
+        for (; l < m; ++l) acc[0] = __dadd_rn(acc[0], pow_abs(static_cast<double>(xi[l]) - static_cast<double>(xj[l]), a.p));
     } else {
         const double mi = a.mu[i], mj = a.mu[j];
-        const double si = 1.0 / sqrt(a.S[i] / a.m), sj = 1.0 / sqrt(a.S[j] / a.m);
-        for (int l = 0; l < a.m; ++l) {
-            const double d = (static_cast<double>(xi[l]) - mi) * si - (static_cast<double>(xj[l]) - mj) * sj;
-            acc = fma(d, d, acc);
+        const double si = 1.0 / sqrt(a.S[i] / m), sj = 1.0 / sqrt(a.S[j] / m);
+        int l = 0;
+        for (; l + 4 <= m; l += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double d = __dsub_rn(__dmul_rn(static_cast<double>(xi[l + u]) - mi, si),
+                                           __dmul_rn(static_cast<double>(xj[l + u]) - mj, sj));
+                acc[u] = fma(d, d, acc[u]);
+            }
+        }
+        for (; l < m; ++l) {
+            const double d = __dsub_rn(__dmul_rn(static_cast<double>(xi[l]) - mi, si),
+                                       __dmul_rn(static_cast<double>(xj[l]) - mj, sj));
+            acc[0] = fma(d, d, acc[0]);
         }
     }
-    return acc;
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
 template <typename X>
