@@ -158,6 +158,19 @@ def test_invalid_arguments(mp):
         mp.aamp(Tt, 10, -1)
     with pytest.raises(mp.MPError):
         mp.acamp(Tt, 1, 0)
+    # a rejected call launches nothing and leaves the outputs as they were
+    P = torch.full((91,), 7.5, dtype=torch.float64, device="cuda")
+    I = torch.full((91,), 3, dtype=torch.int64, device="cuda")
+    lib = mp.load()
+    n0 = lib.mp_launch_count()
+    for bad in (dict(excl=-1), dict(variant=9), dict(precision="fp64", variant=mp.MP_VARIANT_FAST)):
+        kw = dict(excl=2)
+        kw.update(bad)
+        with pytest.raises(mp.MPError):
+            mp.aamp(Tt, 10, kw.pop("excl"), out=(P, I), **kw)
+    torch.cuda.synchronize()
+    assert lib.mp_launch_count() == n0
+    assert torch.all(P == 7.5) and torch.all(I == 3)
 
 
 @pytest.mark.parametrize("m", [32, 64, 96])
