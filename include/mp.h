@@ -228,7 +228,11 @@ typedef struct mp_batch_plan mp_batch_plan;
  * belongs to the current device.  opt may be NULL; the batch runs the FP32
  * sweep with the default re-anchor interval and whole diagonal ranges, so
  * opt->precision must be MP_PREC_FP32, reanchor 0, k_begin = k_end = 0 (else
- * MP_ERR_UNSUPPORTED); opt->polish is honoured.  desc is not kept.
+ * MP_ERR_UNSUPPORTED); opt->polish is honoured; opt->variant may be AUTO or
+ * FAST (no block filter) or FAST_FILTER (the filter on the Euclidean
+ * two-stream queue).  The tile queues take the series in turn (first tiles of
+ * all series, then second tiles, ...), longest tiles first within a turn.
+ * desc is not kept.
  * Errors: MP_ERR_INVALID_ARG (desc, sizes, dist, p), MP_ERR_UNSUPPORTED
  * (dtype, options, N_s >= 2^31, more than 2^32 - 1 tiles in a queue, m_s too
  * large for shared memory), MP_ERR_CUDA (allocation or copy failed; nothing

@@ -678,6 +678,7 @@ struct mp_batch_plan {
     double p = 2.0;
     int polish = 1;
     int genp_kind = mpk::K_P2;  // exponent kind of the p-norm queues
+    bool filter = false;        // the p = 2 two-stream queue runs the block filter
     long long windows = 0, zwindows = 0, samples = 0;
     std::vector<mpk::BatchSeries> series;
     std::vector<long long> w_start;
@@ -715,17 +716,19 @@ void batch_free(mp_batch_plan *pl) {
 }
 
 // Tiles of one series for a sweep whose bands hold KW diagonals and whose
-// tiles hold R rows (band b: L - b KW rows), with cost = rows x diagonals.
+// tiles hold R rows (band b: L - b KW rows), with cost = rows x diagonals and
+// the tile's rank within its series (band-major) in the spare field.
 void batch_tiles(std::vector<std::pair<long long, mpk::BatchTile>> &out, int s, long long L, int KW, int R) {
     if (L <= 0) return;
     const long long nb = (L + KW - 1) / KW;
+    int rank = 0;
     for (long long b = 0; b < nb; ++b) {
         const long long Lb = L - b * KW;
         const long long nd = std::min<long long>(KW, Lb);
         const long long nt = (Lb + R - 1) / R;
         for (long long rt = 0; rt < nt; ++rt) {
             const long long rows = std::min<long long>(R, Lb - rt * R);
-            out.push_back({rows * nd, mpk::BatchTile{s, static_cast<int>(b), static_cast<int>(rt), 0}});
+            out.push_back({rows * nd, mpk::BatchTile{s, static_cast<int>(b), static_cast<int>(rt), rank++}});
         }
     }
 }
@@ -751,6 +754,8 @@ mp_status batch_validate(const mp_batch_desc *d, const mp_options *opt, mp_optio
     if (o.reanchor != 0) return fail(MP_ERR_UNSUPPORTED, "batches use the default re-anchor interval");
     if (o.k_begin != 0 || o.k_end != 0) return fail(MP_ERR_UNSUPPORTED, "batches sweep whole diagonal ranges");
     if (o.polish != 0 && o.polish != 1) return fail(MP_ERR_INVALID_ARG, "polish %d", o.polish);
+    if (o.variant != MP_VARIANT_AUTO && o.variant != MP_VARIANT_FAST && o.variant != MP_VARIANT_FAST_FILTER)
+        return fail(MP_ERR_UNSUPPORTED, "batches take variant AUTO, FAST or FAST_FILTER");
     if (d->t_offsets[0] < 0) return fail(MP_ERR_INVALID_ARG, "t_offsets[0] < 0");
     bool any_p = false;
     for (int s = 0; s < d->num_series; ++s) {
@@ -786,11 +791,11 @@ cudaError_t launch_gen_batch(const mp_batch_plan *pl, const mpk::BatchData &bd, 
     return cudaGetLastError();
 }
 
-template <int KIND>
+template <int KIND, bool FILTER>
 cudaError_t fast_batch_attr(mp_batch_plan *pl, int qi, int sms) {
-    cudaError_t e = cudaFuncSetAttribute(mpk::sweep2_batch_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(pl->smem[qi]));
-    if (e == cudaSuccess) batch_grid(pl, qi, mpk::sweep2_batch_kernel<KIND>, mpk::V2_NT, sms);
+    cudaError_t e = cudaFuncSetAttribute(mpk::sweep2_batch_kernel<KIND, FILTER>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(pl->smem[qi]));
+    if (e == cudaSuccess) batch_grid(pl, qi, mpk::sweep2_batch_kernel<KIND, FILTER>, mpk::V2_NT, sms);
     return e;
 }
 
@@ -863,11 +868,12 @@ mp_status batch_build_graph(mp_batch_plan *pl, const void *T, double *P, int64_t
         if (pl->tiles[qi].empty()) continue;
         const mpk::BatchQueue q{pl->d_tiles[qi], static_cast<unsigned>(pl->tiles[qi].size()), tickets + qi};
         if (qi == mp_batch_plan::Q_FAST2)
-            mpk::sweep2_batch_kernel<mpk::K_P2><<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
+            if (pl->filter) mpk::sweep2_batch_kernel<mpk::K_P2, true><<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
+            else mpk::sweep2_batch_kernel<mpk::K_P2, false><<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
         else if (qi == mp_batch_plan::Q_FASTP && pl->genp_kind == mpk::K_P1)
-            mpk::sweep2_batch_kernel<mpk::K_P1><<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
+            mpk::sweep2_batch_kernel<mpk::K_P1, false><<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
         else if (qi == mp_batch_plan::Q_FASTP)
-            mpk::sweep2_batch_kernel<mpk::K_P3><<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
+            mpk::sweep2_batch_kernel<mpk::K_P3, false><<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
         else if (qi == mp_batch_plan::Q_Z)
             mpk::sweepz_batch_kernel<<<pl->grid[qi], mpk::Z_NT, pl->smem[qi], st>>>(bd, q);
         else
@@ -938,6 +944,7 @@ static mp_status batch_plan_build(const mp_batch_desc *desc, const mp_options *o
     pl->S = desc->num_series;
     pl->p = desc->p;
     pl->polish = o.polish;
+    pl->filter = o.variant == MP_VARIANT_FAST_FILTER;
     if (desc->p == 1.0) pl->genp_kind = mpk::K_P1;
     else if (desc->p == 2.0) pl->genp_kind = mpk::K_P2;
     else if (desc->p == 3.0) pl->genp_kind = mpk::K_P3;
@@ -995,9 +1002,15 @@ static mp_status batch_plan_build(const mp_batch_desc *desc, const mp_options *o
             batch_free(pl);
             return fail(MP_ERR_UNSUPPORTED, "more than 2^32 - 2 tiles in one queue");
         }
-        if (seed == 0) {  // longest tiles first; ties in series / band / row order
-            std::stable_sort(q[qi].begin(), q[qi].end(),
-                             [](const auto &a, const auto &b) { return a.first > b.first; });
+        if (seed == 0) {
+            // Round robin over the series (every series' first tile, then every
+            // series' second tile, ...), longest first within a round: the tiles
+            // of one series run one after another, each starting from the
+            // thresholds its predecessors left, instead of all at once with
+            // open thresholds; the ticket queue balances the load whatever the order.
+            std::stable_sort(q[qi].begin(), q[qi].end(), [](const auto &a, const auto &b) {
+                return a.second.rank < b.second.rank || (a.second.rank == b.second.rank && a.first > b.first);
+            });
         } else {  // Fisher-Yates with splitmix64
             unsigned long long st = seed ^ (0x632be59bd9b4e019ull * (qi + 1));
             for (size_t t = q[qi].size(); t > 1; --t) {
@@ -1052,9 +1065,10 @@ static mp_status batch_plan_build(const mp_batch_desc *desc, const mp_options *o
         if (e != cudaSuccess) break;
         if (qi == mp_batch_plan::Q_FAST2 || qi == mp_batch_plan::Q_FASTP) {
             const int kind = qi == mp_batch_plan::Q_FAST2 ? mpk::K_P2 : pl->genp_kind;
-            e = kind == mpk::K_P1 ? fast_batch_attr<mpk::K_P1>(pl, qi, sms)
-                : kind == mpk::K_P3 ? fast_batch_attr<mpk::K_P3>(pl, qi, sms)
-                                    : fast_batch_attr<mpk::K_P2>(pl, qi, sms);
+            e = kind == mpk::K_P1 ? fast_batch_attr<mpk::K_P1, false>(pl, qi, sms)
+                : kind == mpk::K_P3 ? fast_batch_attr<mpk::K_P3, false>(pl, qi, sms)
+                : pl->filter        ? fast_batch_attr<mpk::K_P2, true>(pl, qi, sms)
+                                    : fast_batch_attr<mpk::K_P2, false>(pl, qi, sms);
         } else if (qi == mp_batch_plan::Q_Z) {
             e = cudaFuncSetAttribute(mpk::sweepz_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(pl->smem[qi]));
@@ -1472,12 +1486,14 @@ mp_status mp_anytime_run(mp_anytime *a, int64_t max_tiles, void *stream) {
     const mpk::BatchData bd = anytime_data(a, nullptr, nullptr);
     const mpk::BatchQueue q{pl->d_tiles[qi] + a->cursor, static_cast<unsigned>(count), ticket};
     const int grid = static_cast<int>(std::min<long long>(pl->grid[qi], count));
-    if (qi == mp_batch_plan::Q_FAST2)
-        mpk::sweep2_batch_kernel<mpk::K_P2><<<grid, mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
+    if (qi == mp_batch_plan::Q_FAST2 && pl->filter)
+        mpk::sweep2_batch_kernel<mpk::K_P2, true><<<grid, mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
+    else if (qi == mp_batch_plan::Q_FAST2)
+        mpk::sweep2_batch_kernel<mpk::K_P2, false><<<grid, mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
     else if (qi == mp_batch_plan::Q_FASTP && pl->genp_kind == mpk::K_P1)
-        mpk::sweep2_batch_kernel<mpk::K_P1><<<grid, mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
+        mpk::sweep2_batch_kernel<mpk::K_P1, false><<<grid, mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
     else if (qi == mp_batch_plan::Q_FASTP)
-        mpk::sweep2_batch_kernel<mpk::K_P3><<<grid, mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
+        mpk::sweep2_batch_kernel<mpk::K_P3, false><<<grid, mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
     else if (qi == mp_batch_plan::Q_Z)
         mpk::sweepz_batch_kernel<<<grid, mpk::Z_NT, pl->smem[qi], st>>>(bd, q);
     else {

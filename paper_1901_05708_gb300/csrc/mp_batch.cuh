@@ -9,9 +9,9 @@
 //   batch_zstats    FP64 window statistics of the z-normalised series
 //   batch_zoperands FP32 operands of the centred-covariance sweep
 //   *_batch_kernel  persistent CTAs take tiles from a queue (one atomic
-//                   ticket per tile); the queue lists the tiles of every
-//                   series in order of decreasing cell count, so the long
-//                   tiles start first and the short ones fill the tail
+//                   ticket per tile); the queue takes the series in turn
+//                   (first tiles of all series, then second tiles, ...),
+//                   longest first within a turn
 //   batch_finalize  keys -> P, I (FP64 polish)
 // One queue per sweep kernel: the two-stream sweep (m a multiple of 32) for
 // p = 2 and for the batch's p-norm exponent when it is 1 or 3, the
@@ -41,7 +41,8 @@ struct BatchSeries {
 };
 
 struct BatchTile {
-    int series, band, rt, pad;
+    int series, band, rt;
+    int rank;  // position among its series' tiles (queue order only)
 };
 
 struct BatchQueue {
@@ -143,7 +144,7 @@ __device__ __forceinline__ bool batch_next(const BatchQueue &q, const BatchData 
     return true;
 }
 
-template <int KIND>
+template <int KIND, bool FILTER>
 __global__ void __launch_bounds__(V2_NT, 2) sweep2_batch_kernel(const BatchData d, const BatchQueue q) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Sweep2Args sa;
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(V2_NT, 2) sweep2_batch_kernel(const BatchData 
             sa.B = sr->m / V2_QMAX;
         }
         __syncthreads();
-        sweep2_tile<KIND, false>(sa, tile.band, tile.rt, smem);
+        sweep2_tile<KIND, FILTER>(sa, tile.band, tile.rt, smem);
         __syncthreads();
     }
 }

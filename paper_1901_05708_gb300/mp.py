@@ -300,7 +300,7 @@ class BatchPlan:
     I within the series.  The plan keeps its workspace, so that repeated runs
     with the same output buffers replay the same graph."""
 
-    def __init__(self, lengths, m, dist, excl, p: float = 2.0, polish: bool = True, device=None):
+    def __init__(self, lengths, m, dist, excl, p: float = 2.0, polish: bool = True, device=None, variant: int = 0):
         import numpy as np
         lib = load()
         self._desc, keep = batch_desc(lengths, m, dist, excl, p)
@@ -311,7 +311,7 @@ class BatchPlan:
         np.cumsum(N, out=self.out_offsets[1:])
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index)
-        opt = options(polish=polish)
+        opt = options(polish=polish, variant=variant)
         h = ctypes.c_void_p()
         nbytes = ctypes.c_size_t()
         with torch.cuda.device(self.device):
