@@ -151,7 +151,7 @@ __host__ __device__ __forceinline__ int v2_cpos(int x) { return x + (x >> 3); }
 
 inline size_t sweep2_smem_bytes(int m, int Q) {
     const size_t nj = v2_jpos(V2_KW + V2_H + m + 16) + 2;
-    const size_t ni = V2_H + m + 16;
+    const size_t ni = V2_H + m + 16 + 2;  // + the one-element shift of IT, kept even
     const size_t nc = v2_cpos(V2_KW + 2 * V2_H + 16);
     return (nj + ni) * sizeof(float2) + (2 * V2_H + 4 + nc) * sizeof(float) +
            static_cast<size_t>(Q) * V2_D * V2_NT * sizeof(float2);
@@ -262,10 +262,12 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
     //  thr_c[cpos(x)]          threshold of column r0 + k0 + x
     const int njs = v2_jpos(V2_KW + V2_H + m + 16) + 2;
     float2 *JT = reinterpret_cast<float2 *>(smem);
-    float2 *IT = JT + njs;
+    // IT sits one element past a 16-byte boundary, so that the pairs of rows
+    // (8g+1, 8g+2), (8g+3, 8g+4), ... are 16-byte loads (m is a multiple of 32)
+    float2 *IT = JT + njs + 1;
     // thr_r is offset by 3 floats from a 16-byte boundary, so that the
     // thresholds of rows 8g+1 .. 8g+4 and 8g+5 .. 8g+8 are 16-byte loads
-    float *thr_r = reinterpret_cast<float *>(IT + (V2_H + m + 16)) + 3;
+    float *thr_r = reinterpret_cast<float *>(JT + njs + (V2_H + m + 16 + 2)) + 3;
     float *thr_c = thr_r + 2 * V2_H + 1;
     float2 *ring = reinterpret_cast<float2 *>(thr_c + v2_cpos(V2_KW + 2 * V2_H + 16));
 
@@ -465,10 +467,14 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
             const int slot0 = anchor_slot, next0 = next_anchor;
             float bma = NONE, bmb = NONE;
             {
-                const float2 *itl0 = IT + ub, *ite0 = IT + ub + m;
+                const float4 *itl4 = reinterpret_cast<const float4 *>(IT + ub + 1);
+                const float4 *ite4 = reinterpret_cast<const float4 *>(IT + ub + m + 1);
 #pragma unroll
                 for (int ul = 1; ul <= V2_D; ++ul) {
-                    step(ul == V2_D && anc, itl0[ul], ite0[ul], WL, WE, ul);
+                    const float4 l4 = itl4[(ul - 1) >> 1], e4 = ite4[(ul - 1) >> 1];
+                    const float2 tl = (ul & 1) ? make_float2(l4.x, l4.y) : make_float2(l4.z, l4.w);
+                    const float2 te = (ul & 1) ? make_float2(e4.x, e4.y) : make_float2(e4.z, e4.w);
+                    step(ul == V2_D && anc, tl, te, WL, WE, ul);
 #pragma unroll
                     for (int d = 0; d < V2_D; d += 2) {
                         bma = min3f(bma, s[d].x, s[d + 1].x);
@@ -534,16 +540,18 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
             // per-block bases, so that every access below uses a constant offset
             const float *tra = thr_r + ub, *trb = thr_r + V2_H + ub;
             float *tca = thr_c + v2_cpos(jb + ub), *tcb = thr_c + v2_cpos(jb + Ht + ub);  // jb + ub, Ht: multiples of 8
-            const float2 *itl = IT + ub, *ite = IT + ub + m;
+            const float4 *itl4 = reinterpret_cast<const float4 *>(IT + ub + 1);
+            const float4 *ite4 = reinterpret_cast<const float4 *>(IT + ub + m + 1);
 #pragma unroll
             for (int pr = 0; pr < V2_D / 2; ++pr) {
                 const int ul0 = 2 * pr + 1, ul1 = ul0 + 1;  // rows u0 = ub + ul0, u1 = ub + ul1
                 const int cp0 = ul0 + (ul0 >> 3), cp1 = ul1 + (ul1 >> 3);  // padded column offsets
                 float t0a[V2_D], t0b[V2_D], t1a[V2_D], t1b[V2_D];
-                step(false, itl[ul0], ite[ul0], WL, WE, ul0);
+                const float4 l4 = itl4[pr], e4 = ite4[pr];  // rows ul0 and ul1
+                step(false, make_float2(l4.x, l4.y), make_float2(e4.x, e4.y), WL, WE, ul0);
                 v2_tag8(t0a, s, false, tag_mask);
                 v2_tag8(t0b, s, true, tag_mask);
-                step(pr == V2_D / 2 - 1 && anc, itl[ul1], ite[ul1], WL, WE, ul1);
+                step(pr == V2_D / 2 - 1 && anc, make_float2(l4.z, l4.w), make_float2(e4.z, e4.w), WL, WE, ul1);
                 v2_tag8(t1a, s, false, tag_mask);
                 v2_tag8(t1b, s, true, tag_mask);
                 const float r0a = v2_min8(t0a), r0b = v2_min8(t0b), r1a = v2_min8(t1a), r1b = v2_min8(t1b);
