@@ -72,8 +72,10 @@ typedef enum { MP_DIST_EUCLID = 0, MP_DIST_PNORM = 1, MP_DIST_ZNORM = 2 } mp_dis
  * one FP32 kernel).  AUTO: the two-stream kernel where it applies (FP32
  * input, m a multiple of 32, p in {1, 2, 3}, default re-anchor interval),
  * with the block filter for p = 2 and N >= 200,000; else, for m >= 512 and
- * p in {1, 2, 3} (or where the generic kernel's shared memory does not fit
- * m), the tall-tile kernel; else the generic kernel.
+ * p in {1, 2, 3} with float32 input (or where the generic kernel's shared
+ * memory does not fit m), the tall-tile kernel; else the generic kernel.
+ * (The tall kernel does not re-anchor within a tile, so for short windows its
+ * FP32 rounding grows past the tolerance, most for p = 3.)
  * The others force a choice (MP_ERR_UNSUPPORTED where it does not apply);
  * mp_autotune times them. */
 typedef enum {
@@ -350,7 +352,7 @@ mp_status mp_anytime_destroy(mp_anytime *a);
  * two-stream kernel with and without the filter; the generic kernel at its
  * default re-anchor interval and at intervals of 16, 32 and 64 rows that
  * divide m into at most 8 blocks, each distinct interval once; the tall-tile
- * kernel)
+ * kernel for m >= 512)
  * on the caller's series, each candidate once to warm up and once timed (the
  * sweep kernel alone, CUDA events on `stream`; the call synchronises it).
  * slice_cells = 0 times the whole sweep; slice_cells > 0 only the first

@@ -339,6 +339,13 @@ bool tall_applies(const Problem &pb) {
 bool use_tall(const Problem &pb) {
     if (pb.opt.variant == MP_VARIANT_TALL) return true;
     if (pb.opt.variant != MP_VARIANT_AUTO || !tall_applies(pb) || getenv_generic()) return false;
+    // The tall kernel carries a whole tile without re-anchoring: the rounding of
+    // each step's increment accumulates over up to S/2 rows.  An increment is
+    // about 1/m of a window sum, so from m = 512 on that stays well inside the
+    // FP32 tolerance; for shorter windows (where the tall kernel would be about
+    // twice as fast: m = 40 .. 500, p = 1 and 2, measured) the generic kernel's
+    // exact re-anchoring every B <= 64 rows keeps p = 3 and near matches exact
+    // enough (the tall kernel failed the tolerance at m = 5 and 24 for p = 3).
     return generic_smem(pb) == 0 || (pb.m >= 512 && pb.dtype == MP_F32);
 }
 
@@ -1643,7 +1650,8 @@ mp_status mp_autotune(int dist, const void *T, int dtype, int64_t n, int32_t m, 
             g.opt.reanchor = target;
             if (generic_smem(g) > 0) cands[nc++] = {MP_VARIANT_GENERIC, target};
         }
-        if (tall_applies(pb)) cands[nc++] = {MP_VARIANT_TALL, 0};
+        // the tall kernel only where its accuracy holds (see use_tall)
+        if (tall_applies(pb) && (pb.m >= 512 || generic_smem(pb) == 0)) cands[nc++] = {MP_VARIANT_TALL, 0};
     }
     if (nc <= 1) {  // nothing to choose
         if (nc == 1) {

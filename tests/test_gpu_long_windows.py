@@ -72,7 +72,7 @@ def test_window_beyond_the_generic_kernel(mp):
 
 
 def test_tall_kernel_on_short_windows(mp):
-    """The forced tall kernel on m = 64 agrees with the default (two-stream) kernel."""
+    """The forced tall kernel on m = 64 (p = 2) agrees with the default (two-stream) kernel."""
     s = W.small("walk", 50_000, 64, 64, dtype=np.float32)
     Pt, It = run(mp, s.T, s.m, s.excl, "euclid", variant=4)
     Pd, Id = run(mp, s.T, s.m, s.excl, "euclid")
