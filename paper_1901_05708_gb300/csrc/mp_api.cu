@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "mp.h"
+#include <nvtx3/nvToolsExt.h>
 #include "mp_device.cuh"
 #include "mp_prep.cuh"
 #include "mp_sweep.cuh"
@@ -35,6 +36,13 @@ std::atomic<unsigned long long> g_launches{0};
 
 // Count one kernel launch of this library (reported by mp_launch_count).
 inline void counted(int n = 1) { g_launches.fetch_add(static_cast<unsigned long long>(n)); }
+
+// NVTX range over one stage of a call (seen by profilers that record NVTX;
+// otherwise a no-op).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 // Bracket the sweep kernel with the caller's profiling events, if set.
 struct SweepEvents {
@@ -411,7 +419,11 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
     cudaGetLastError();  // clear a stale launch error of an unrelated caller
 
     const bool f64 = pb.opt.precision == MP_PREC_FP64;
-    s = pb.dtype == MP_F64 ? prep_series<double>(pb, L, T, w, st) : prep_series<float>(pb, L, T, w, st);
+    Range call_range(pb.dist == MP_DIST_EUCLID ? "mp_aamp" : pb.dist == MP_DIST_PNORM ? "mp_pnorm" : "mp_acamp");
+    {
+        Range r("a1 convert");
+        s = pb.dtype == MP_F64 ? prep_series<double>(pb, L, T, w, st) : prep_series<float>(pb, L, T, w, st);
+    }
     if (s != MP_OK) return s;
     if (f64) {
         mpk::fill_u64_kernel<<<grid_for(2 * pb.N, mpk::PREP_NT), mpk::PREP_NT, 0, st>>>(
@@ -424,6 +436,7 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
     }
     const double *x64 = reinterpret_cast<const double *>(w + L.x64);
     if (pb.dist == MP_DIST_ZNORM) {
+        Range r("a2 window statistics");
         mpk::window_stats_kernel<<<grid_for(pb.N, mpk::PREP_NT), mpk::PREP_NT, 0, st>>>(
             x64, pb.N, pb.m, reinterpret_cast<double *>(w + L.mu), reinterpret_cast<double *>(w + L.S),
             reinterpret_cast<unsigned char *>(w + L.flat));
@@ -440,6 +453,7 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
         }
     }
     if (pb.k_first < pb.k_end) {
+        Range r("a3-a5 sweep");
         if (pb.dist == MP_DIST_ZNORM || f64) {
             const mpk::TileGrid g = mpk::make_grid(pb.N, pb.k_first, pb.k_end, mpk::SM_KW, mpk::SM_KW);
             if (g.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", g.tiles);
@@ -498,6 +512,7 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
             if (s != MP_OK) return s;
         }
     }
+    Range fin_range("a6 finalize");
     mpk::FinalizeArgs fa{};
     fa.keys = f64 ? nullptr : reinterpret_cast<const unsigned long long *>(w + L.keys);
     fa.keys128 = f64 ? reinterpret_cast<const mpk::Key128 *>(w + L.keys128) : nullptr;
