@@ -92,6 +92,24 @@ def test_replay_and_rebuild(mp):
     plan.close()
 
 
+def test_filter_variant_gives_the_same_profile(mp):
+    """MP_VARIANT_FAST_FILTER only skips candidates that cannot pass: bit-identical results."""
+    series = mixed_batch(13, 1.0)
+    lengths, ms = [s.n for s in series], [s.m for s in series]
+    dists, excls = [s.dist for s in series], [s.excl for s in series]
+    T = torch.from_numpy(np.concatenate([s.T for s in series]).astype(np.float32)).cuda()
+    a = mp.BatchPlan(lengths, ms, dists, excls, p=1.0)
+    b = mp.BatchPlan(lengths, ms, dists, excls, p=1.0, variant=mp.MP_VARIANT_FAST_FILTER)
+    Pa, Ia = a.run(T)
+    Pb, Ib = b.run(T)
+    torch.cuda.synchronize()
+    assert torch.equal(Pa, Pb) and torch.equal(Ia, Ib)
+    with pytest.raises(mp.MPError):
+        mp.BatchPlan(lengths, ms, dists, excls, p=1.0, variant=mp.MP_VARIANT_GENERIC)
+    a.close()
+    b.close()
+
+
 def test_polish_off_keeps_sweep_values(mp):
     """polish = 0: same neighbours, P is the sweep's own FP32 value (for the
     z-normalised series q = 1 - rho carries an absolute FP32 error)."""
