@@ -28,12 +28,13 @@
 //    that passes its threshold costs two atomics and nothing else.
 //
 //  * Block filter (FILTER, for p = 2 on long series).  Each 8-row block first
-//    runs the recurrence with one running minimum per stream; unless some
-//    lane of the warp could beat the loosest threshold of the rows and
-//    columns its block feeds, the block is done without tags or slots.
-//    Otherwise the block is replayed from the saved state with the tracked
-//    bookkeeping above, and the next blocks skip the filter for a number of
-//    blocks that doubles while it keeps failing.
+//    runs the recurrence of E and F' alone and bounds the scores of each
+//    group of V2_LBR rows from below by E(row before the group) - F'(last row
+//    of the group), per diagonal (both sums only grow within a block); unless
+//    some lane's bound could beat the loosest threshold of the rows and
+//    columns its block feeds, the block is done without scores, tags or
+//    slots.  Otherwise the block is replayed from the saved state with the
+//    tracked bookkeeping above.
 //
 //  * Shared memory holds, per tile, the j-side series as float2 pairs
 //    (stream a, stream b) padded by 16 bytes every 64 so that each lane's
@@ -54,6 +55,7 @@ constexpr int V2_D = 8;                // diagonals per thread
 constexpr int V2_KW = V2_NT * V2_D;    // diagonals per band
 constexpr int V2_H = 1024;             // rows per stream
 constexpr int V2_R = 2 * V2_H;         // rows per tile
+constexpr int V2_LBR = 4;              // filter pass: rows per lower bound (divides V2_D)
 constexpr int V2_QMAX = 4;             // ring blocks per diagonal
 // shared memory of one CTA such that two fit on an SM (228 KB, 1 KB reserved per CTA)
 constexpr size_t V2_SMEM_MAX = 113 * 1024;
@@ -428,13 +430,15 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
 
     // ---- fast region: 8-row blocks (ub, ub + 8] with every cell valid --------------
     int ub = 0;
-    int skip = 0, backoff = 1;  // blocks to run tracked without a filter pass; next skip length
     bool group_valid = false;   // gca, gcb hold the column maxima for this block's columns 1..8
     float gca = NONE, gcb = NONE;
     constexpr bool kFilter = FILTER;
     for (; ub + V2_D < ufast; ub += V2_D) {
+        // j-side samples of the block's leaving and entering windows; loaded
+        // by each pass that uses them (the filter pass and, when it runs, the
+        // tracked pass), so that they are not held across the filter decision
         float2 WL[2 * V2_D], WE[2 * V2_D];
-        {
+        auto load_w = [&]() {
             const int qL = 5 * ((jb + ub) >> 3), qE = 5 * ((jb + ub + m) >> 3);
 #pragma unroll
             for (int q = 0; q < V2_D; ++q) {
@@ -445,40 +449,70 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
                 WE[2 * q] = make_float2(e4.x, e4.y);
                 WE[2 * q + 1] = make_float2(e4.z, e4.w);
             }
-        }
+        };
         const bool anc = ub + V2_D == next_anchor;  // B % 8 == 0: anchors fall on a block's last row
-        // ---- filter pass (p = 2): the recurrence and one running minimum
-        // over the block's 128 scores.  In the steady state no score of the
-        // block reaches the loosest threshold of the rows and columns it feeds,
-        // and the block costs the recurrence plus half an instruction per
-        // cell.  The decision is taken for the warp's active lanes together
-        // (one lane that needs the tracked pass costs the warp that pass
-        // anyway); after a failed filter the next blocks go straight to the
-        // tracked pass, for a number of blocks that doubles while the filter
-        // keeps failing.
+        // ---- filter pass (p = 2): the recurrence of E and F' and lower
+        // bounds for the block's scores.  In the steady state no bound reaches
+        // the loosest threshold of the rows and columns the block feeds, and
+        // the block costs four packed operations per cell pair plus two per
+        // diagonal and group.  The decision is taken for the warp's active
+        // lanes together (one lane that needs the tracked pass costs the warp
+        // that pass anyway).  Every block is filtered: sending the blocks after
+        // a failure straight to the tracked pass measured slower on random
+        // walks and on i.i.d. data alike.
         bool track = true;
-        if (kFilter && skip > 0) {
-            --skip;
-            group_valid = false;
-        } else if (kFilter) {
+        if (kFilter) {
             float2 E0[V2_D], F0[V2_D];
 #pragma unroll
             for (int d = 0; d < V2_D; ++d) { E0[d] = E[d]; F0[d] = F[d]; }
             const int slot0 = anchor_slot, next0 = next_anchor;
+            // Within the block E and F' only grow (every step adds a term >= 0,
+            // and rounding is monotone), so for a group of rows g+1 .. g+G,
+            // E(g) - F'(g+G) is at most each of their scores s = E - F': one
+            // subtraction per diagonal and group bounds G rows, and the pass
+            // needs neither s nor per-cell minima.  The bound is loose by at
+            // most G terms of the sums.  An anchor row (the block's last)
+            // restarts E and F'; there the last group's other rows are bounded
+            // with F' before the anchor and the anchor row by its exact value.
+            load_w();
             float bma = NONE, bmb = NONE;
+            auto fold = [&](float2 x0, float2 x1) {
+                bma = min3f(bma, x0.x, x1.x);
+                bmb = min3f(bmb, x0.y, x1.y);
+            };
             {
                 const float4 *itl4 = reinterpret_cast<const float4 *>(IT + ub + 1);
                 const float4 *ite4 = reinterpret_cast<const float4 *>(IT + ub + m + 1);
+                float2 Eg[V2_D];  // E at the row before the current group
+#pragma unroll
+                for (int d = 0; d < V2_D; ++d) Eg[d] = E0[d];
 #pragma unroll
                 for (int ul = 1; ul <= V2_D; ++ul) {
                     const float4 l4 = itl4[(ul - 1) >> 1], e4 = ite4[(ul - 1) >> 1];
                     const float2 tl = (ul & 1) ? make_float2(l4.x, l4.y) : make_float2(l4.z, l4.w);
                     const float2 te = (ul & 1) ? make_float2(e4.x, e4.y) : make_float2(e4.z, e4.w);
-                    step(ul == V2_D && anc, tl, te, WL, WE, ul);
+                    if (ul == V2_D && anc) {
+                        if (V2_LBR > 1) {
 #pragma unroll
-                    for (int d = 0; d < V2_D; d += 2) {
-                        bma = min3f(bma, s[d].x, s[d + 1].x);
-                        bmb = min3f(bmb, s[d].y, s[d + 1].y);
+                            for (int d = 0; d < V2_D; d += 2) fold(v2_sub(Eg[d], F[d]), v2_sub(Eg[d + 1], F[d + 1]));
+                        }
+                        step(true, tl, te, WL, WE, ul);
+#pragma unroll
+                        for (int d = 0; d < V2_D; d += 2) fold(s[d], s[d + 1]);
+                    } else {
+#pragma unroll
+                        for (int d = 0; d < V2_D; ++d) {
+                            E[d] = v2_acc<KIND>(v2_sub(te, WE[ul + d]), E[d]);
+                            F[d] = v2_acc<KIND>(v2_sub(tl, WL[ul + d]), F[d]);
+                        }
+                        if (ul % V2_LBR == 0) {
+#pragma unroll
+                            for (int d = 0; d < V2_D; d += 2) fold(v2_sub(Eg[d], F[d]), v2_sub(Eg[d + 1], F[d + 1]));
+                            if (ul < V2_D) {
+#pragma unroll
+                                for (int d = 0; d < V2_D; ++d) Eg[d] = E[d];
+                            }
+                        }
                     }
                 }
             }
@@ -529,14 +563,11 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
                 for (int d = 0; d < V2_D; ++d) { E[d] = E0[d]; F[d] = F0[d]; }
                 anchor_slot = slot0;
                 next_anchor = next0;
-                skip = backoff;
-                backoff = backoff < 32 ? 2 * backoff : 32;
-            } else {
-                backoff = 1;
             }
         }
         if (track) {
             // ---- tracked pass of the block
+            load_w();
             // per-block bases, so that every access below uses a constant offset
             const float *tra = thr_r + ub, *trb = thr_r + V2_H + ub;
             float *tca = thr_c + v2_cpos(jb + ub), *tcb = thr_c + v2_cpos(jb + Ht + ub);  // jb + ub, Ht: multiples of 8
