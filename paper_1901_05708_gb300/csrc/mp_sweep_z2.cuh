@@ -405,15 +405,41 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
 #pragma unroll
                     for (int ul = 1; ul <= Z_D; ++ul) {
                         step(ulb + ul, WF, WG, ul);
+                        if constexpr (ZN) {
+                            // q = 1 + (ch + cl) inv_i inv_j and inv_i > 0 is common to the
+                            // row: its minimum is 1 + inv_i min_d (ch + cl) inv_j, two packed
+                            // operations per cell pair instead of three (flat windows have
+                            // inv = NaN, which the minima skip)
+                            float rma = NONE, rmb = NONE;
 #pragma unroll
-                        for (int d = 0; d < Z_D; d += 2) {
-                            const float2 iI = ZN ? II[ulb + ul] : ONE;
-                            const float2 qa = score(iI, WI[ul + d], d);
-                            const float2 qb = score(iI, WI[ul + d + 1], d + 1);
-                            bma = min3f(bma, qa.x, qb.x);
-                            bmb = min3f(bmb, qa.y, qb.y);
+                            for (int d = 0; d < Z_D; d += 2) {
+                                const float2 va = fma2(cl[d], WI[ul + d], z_mul(ch[d], WI[ul + d]));
+                                const float2 vb = fma2(cl[d + 1], WI[ul + d + 1], z_mul(ch[d + 1], WI[ul + d + 1]));
+                                rma = min3f(rma, va.x, vb.x);
+                                rmb = min3f(rmb, va.y, vb.y);
+                            }
+                            const float2 iI = II[ulb + ul];
+                            bma = fminf(bma, fmaf(rma, iI.x, 1.f));
+                            bmb = fminf(bmb, fmaf(rmb, iI.y, 1.f));
+                        } else {
+#pragma unroll
+                            for (int d = 0; d < Z_D; d += 2) {
+                                const float2 qa = score(ONE, ONE, d);
+                                const float2 qb = score(ONE, ONE, d + 1);
+                                bma = min3f(bma, qa.x, qb.x);
+                                bmb = min3f(bmb, qa.y, qb.y);
+                            }
                         }
                         if ((ul & 1) == 0) renorm();
+                    }
+                    if constexpr (ZN) {
+                        // the row form rounds differently from the tracked pass's q
+                        // (by a few units in the last place of q) and the tags move a
+                        // score by up to 7 units: lower the minimum by more than both
+                        // (NONE, the minimum of an all-flat block, becomes NaN and
+                        // passes no test)
+                        bma = bma - fmaxf(2e-5f, fabsf(bma) * 0x1p-18f);
+                        bmb = bmb - fmaxf(2e-5f, fabsf(bmb) * 0x1p-18f);
                     }
                     float tma = max3f(tra[1], tra[2], tra[3]), tmb = max3f(trb[1], trb[2], trb[3]);
                     tma = max3f(tma, tra[4], tra[5]);
