@@ -8,9 +8,10 @@
 //   q = 1 - rho = 1 - cov inv_i inv_j          (DZ^2 = 2 m q, Lemma 3).
 // FP32 cannot hold cov to the 1e-9 relative that q ~ 0.01 needs over
 // thousands of steps, so cov is a float-float pair (hi, lo): each step adds
-// its increment to the low word (one packed operation) and an error-free
-// Fast2Sum folds the low word into the high word every second row: 7.5
-// packed f32x2 operations per cell pair.
+// its two products to the low word (two chained packed FMAs; the words hold
+// -cov and df is staged negated) and an error-free Fast2Sum folds the low
+// word into the high word every second row: 6.5 packed f32x2 operations per
+// cell pair with the score.
 //
 // Tiles are tall (a band of KW diagonals by up to S rows, split into two row
 // streams packed in f32x2 as in the Euclidean fast path), so the anchor of
@@ -237,15 +238,17 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
             auto gv = [&](const float *p, long long g) -> float { return (g >= 0 && g < a.N) ? p[g] : 0.f; };
             const long long ia = r0 + u0c, ib = rb + u0c;
             if constexpr (ZN) {
+                // df is staged negated (j side and i side), so that the covariance
+                // step is two chained FMAs into the low word
                 for (int x = tid; x < Z_KW + Z_RC + 16; x += Z_NT) {
                     const int px = v2_jpos(x);
-                    JF[px] = make_float2(gv(a.df, ya + x), gv(a.df, yb + x));
+                    JF[px] = make_float2(-gv(a.df, ya + x), -gv(a.df, yb + x));
                     JG[px] = make_float2(gv(a.dg, ya + x), gv(a.dg, yb + x));
                     JI[px] = make_float2(gv(a.inv, ya + x + 1), gv(a.inv, yb + x + 1));
                 }
                 // i side: chunk row ul uses df, dg of window i - 1 and inv of window i
                 for (int ul = tid; ul < Z_RC + 16; ul += Z_NT) {
-                    IF[ul] = make_float2(gv(a.df, ia + ul - 1), gv(a.df, ib + ul - 1));
+                    IF[ul] = make_float2(-gv(a.df, ia + ul - 1), -gv(a.df, ib + ul - 1));
                     IG[ul] = make_float2(gv(a.dg, ia + ul - 1), gv(a.dg, ib + ul - 1));
                     II[ul] = make_float2(gv(a.inv, ia + ul), gv(a.inv, ib + ul));
                 }
@@ -318,9 +321,8 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
             const float2 fi = IF[ul], gi = IG[ul];
 #pragma unroll
             for (int d = 0; d < Z_D; ++d) {
-                if constexpr (ZN) {
-                    const float2 inc = fma2(fi, WG[o + d], z_mul(WF[o + d], gi));  // df_i dg_j + df_j dg_i
-                    cl[d] = v2_sub(cl[d], inc);
+                if constexpr (ZN) {  // cl - df_i dg_j - df_j dg_i (fi, WF hold -df)
+                    cl[d] = fma2(fi, WG[o + d], fma2(WF[o + d], gi, cl[d]));
                 } else {  // + term(e) - term(f), e = t_{i+m-1} - t_{j+m-1}, f = t_{i-1} - t_{j-1}
                     const float2 e = v2_sub(fi, WF[o + d]), f = v2_sub(gi, WG[o + d]);
                     if constexpr (MODE == K_P2) {
