@@ -40,7 +40,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one sweep launch, from a one-pass ncu capture of the
 # current kernel on the full-size workload (profiles/aamp_n1048576_m256_launches.md);
 # None where no capture of the current kernel exists.
-SWEEP_DRAM_BYTES = {("aamp_1m", 1 << 20): 13_370_880 + 161_536}
+SWEEP_DRAM_BYTES = {("aamp_1m", 1 << 20): 13_370_880 + 161_536, ("acamp_1m", 1 << 20): 33_810_176 + 1_842_432}
 
 
 def peaks():
@@ -463,8 +463,10 @@ def main():
                            f"({src} sm_max_mhz) / {instr_per_cell} FP32 instructions per cell",
             "kernel": "diagonal sweep (a3-a5)", "kernel_ms": sweep_avg_ms}
     if traffic is not None:
+        algo = {"aamp_1m": "the series and the keys once, ~12.6 MB",
+                "acamp_1m": "the series, the FP32 operands (df, dg, inv, float-float means) and the keys once, ~32 MB"}
         roof["traffic_note"] = ("bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum); "
-                                "algorithmic: the series and the keys once, ~12.6 MB")
+                                "algorithmic: " + algo[args.workload])
     if clk.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (sms * FP32_LANES_PER_SM * clk["sm_mhz"] * 1e6
                                                      / instr_per_cell / 1e9)
