@@ -45,7 +45,7 @@ constexpr int Z_NT = 128;             // threads per CTA
 constexpr int Z_D = 8;                // diagonals per thread
 constexpr int Z_KW = Z_NT * Z_D;      // diagonals per band
 constexpr int Z_S = 8192;             // rows per tile (at least; S = max(Z_S, 8m) rounded to 2 RC)
-constexpr int Z_RC = 256;             // rows per stream per chunk
+constexpr int Z_RC = 512;             // rows per stream per chunk
 
 // rows per tile for window length m
 __host__ __device__ inline long long z_rows_per_tile(long long m) {
