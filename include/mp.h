@@ -68,20 +68,24 @@ typedef enum {
 
 typedef enum { MP_DIST_EUCLID = 0, MP_DIST_PNORM = 1, MP_DIST_ZNORM = 2 } mp_dist;
 
-/* Kernel of the FP32 Euclidean / p-norm sweep (the z-normalised distance has
- * one FP32 kernel).  AUTO: the two-stream kernel where it applies (FP32
- * input, m a multiple of 32, p in {1, 2, 3}, default re-anchor interval),
- * with the block filter for p = 2 and N >= 200,000; else, for m >= 512 and
- * p in {1, 2, 3} with float32 input (or where the generic kernel's shared
- * memory does not fit m), the tall-tile kernel; else the generic kernel.
- * (The tall kernel does not re-anchor within a tile, so for short windows its
- * FP32 rounding grows past the tolerance, most for p = 3.)
+/* Kernel of the FP32 sweep.  Euclidean / p-norm, AUTO: the two-stream kernel
+ * where it applies (FP32 input, m a multiple of 32, p in {1, 2, 3}, default
+ * re-anchor interval), with the block filter for p = 2 and N >= 200,000; else,
+ * for m >= 512 and p in {1, 2, 3} with float32 input (or where the generic
+ * kernel's shared memory does not fit m), the tall-tile kernel; else the
+ * generic kernel.  (The tall kernel does not re-anchor within a tile, so for
+ * short windows its FP32 rounding grows past the tolerance, most for p = 3.)
+ * The z-normalised distance has one FP32 kernel: AUTO takes its block filter
+ * for N >= 200,000, FAST_FILTER / FAST force it on / off, GENERIC and TALL do
+ * not apply.  The filter only skips candidates that cannot pass, so with or
+ * without it the results are the same bit for bit.
  * The others force a choice (MP_ERR_UNSUPPORTED where it does not apply);
  * mp_autotune times them. */
 typedef enum {
     MP_VARIANT_AUTO = 0,
-    MP_VARIANT_FAST_FILTER = 1,  /* two-stream kernel with the block filter (p = 2) */
-    MP_VARIANT_FAST = 2,         /* two-stream kernel                               */
+    MP_VARIANT_FAST_FILTER = 1,  /* two-stream kernel with the block filter (p = 2); */
+                                 /* z-normalised kernel with its block filter        */
+    MP_VARIANT_FAST = 2,         /* two-stream kernel; z-normalised kernel, no filter */
     MP_VARIANT_GENERIC = 3,      /* generic kernel (any p, input type; reanchor;     */
                                  /* shared memory limits m to about 12,000)          */
     MP_VARIANT_TALL = 4          /* tall-tile kernel: float-float sums, tiles of      */
@@ -352,7 +356,8 @@ mp_status mp_anytime_destroy(mp_anytime *a);
  * two-stream kernel with and without the filter; the generic kernel at its
  * default re-anchor interval and at intervals of 16, 32 and 64 rows that
  * divide m into at most 8 blocks, each distinct interval once; the tall-tile
- * kernel for m >= 512)
+ * kernel for m >= 512; for the z-normalised distance its kernel with and
+ * without the filter)
  * on the caller's series, each candidate once to warm up and once timed (the
  * sweep kernel alone, CUDA events on `stream`; the call synchronises it).
  * slice_cells = 0 times the whole sweep; slice_cells > 0 only the first

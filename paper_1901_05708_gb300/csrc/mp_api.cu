@@ -401,11 +401,14 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
     mp_status s = check_problem(pb, T, P, I, opt);
     if (s != MP_OK) return s;
     const int v = pb.opt.variant;
-    if ((v == MP_VARIANT_FAST || v == MP_VARIANT_FAST_FILTER) &&
+    // the z-normalised distance has one FP32 kernel; FAST / FAST_FILTER choose it
+    // without / with its block filter
+    const bool z32 = pb.dist == MP_DIST_ZNORM && pb.opt.precision == MP_PREC_FP32;
+    if ((v == MP_VARIANT_FAST || v == MP_VARIANT_FAST_FILTER) && !z32 &&
         (pb.opt.precision != MP_PREC_FP32 || pb.dist == MP_DIST_ZNORM || !fast_path_applies(pb)))
         return fail(MP_ERR_UNSUPPORTED, "the two-stream kernel does not apply to this problem");
-    if (v == MP_VARIANT_FAST_FILTER && kind_of(pb.dist, pb.p) != mpk::K_P2)
-        return fail(MP_ERR_UNSUPPORTED, "the block filter exists for p = 2 only");
+    if (v == MP_VARIANT_FAST_FILTER && !z32 && kind_of(pb.dist, pb.p) != mpk::K_P2)
+        return fail(MP_ERR_UNSUPPORTED, "the block filter exists for p = 2 and for the z-normalised kernel");
     if (v == MP_VARIANT_GENERIC && (pb.opt.precision != MP_PREC_FP32 || pb.dist == MP_DIST_ZNORM))
         return fail(MP_ERR_UNSUPPORTED, "the generic kernel is the FP32 Euclidean / p-norm sweep");
     if (v == MP_VARIANT_TALL && !tall_applies(pb))
@@ -488,7 +491,8 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
                 za.tiles = mpk::z_prefix(za.L, za.nb, za.S);
                 if (za.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", za.tiles);
                 const size_t smem = mpk::sweepz_smem_bytes();
-                const bool filter = pb.N >= FILTER_MIN_N;
+                const bool filter = pb.opt.variant == MP_VARIANT_FAST_FILTER ||
+                                    (pb.opt.variant == MP_VARIANT_AUTO && pb.N >= FILTER_MIN_N);
                 auto kern = filter ? mpk::sweepz_kernel<mpk::K_Z, true> : mpk::sweepz_kernel<mpk::K_Z, false>;
                 e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e == cudaSuccess && za.tiles > 0) {
@@ -1667,6 +1671,9 @@ mp_status mp_autotune(int dist, const void *T, int dtype, int64_t n, int32_t m, 
         }
         // the tall kernel only where its accuracy holds (see use_tall)
         if (tall_applies(pb) && (pb.m >= 512 || generic_smem(pb) == 0)) cands[nc++] = {MP_VARIANT_TALL, 0};
+    } else if (pb.dist == MP_DIST_ZNORM && pb.opt.precision == MP_PREC_FP32) {
+        cands[nc++] = {MP_VARIANT_FAST_FILTER, 0};  // the z-normalised kernel with and without its filter
+        cands[nc++] = {MP_VARIANT_FAST, 0};
     }
     if (nc <= 1) {  // nothing to choose
         if (nc == 1) {

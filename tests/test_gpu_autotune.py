@@ -59,3 +59,21 @@ def test_forced_variants_agree(mp):
         mp.pnorm(T, s.m, s.excl, 3.0, variant=1)  # the filter is for p = 2
     with pytest.raises(mp.MPError):
         mp.acamp(T, s.m, s.excl, variant=3)
+
+
+def test_autotune_znorm_filter_choice(mp):
+    """For the z-normalised distance the candidates are its kernel with and
+    without the block filter; the choice runs and matches the oracle."""
+    s = W.small("walk", 210_000, 64, 44, dtype=np.float32)
+    T = torch.from_numpy(s.T).cuda()
+    kw, times = mp.autotune(T, s.m, s.excl, "znorm", force=True)
+    assert kw["variant"] in (mp.MP_VARIANT_FAST_FILTER, mp.MP_VARIANT_FAST)
+    assert len(times) == 2 and all(t > 0 for t in times), times
+    P, I = mp.acamp(T, s.m, s.excl, **kw)
+    torch.cuda.synchronize()
+    rows = np.random.default_rng(5).choice(s.N, 150, replace=False)
+    ref = oracle.brute_rows(s.T, s.m, s.excl, rows, "znorm")
+    parity.check(s.T, s.m, s.excl, "znorm", 2.0, P.cpu().numpy(), I.cpu().numpy(), 1e-5, rows=rows,
+                 P_ref=ref[0], I_ref=ref[1], P2=ref[2], label=f"tuned z {kw}")
+    with pytest.raises(mp.MPError):
+        mp.acamp(T, s.m, s.excl, variant=mp.MP_VARIANT_TALL)

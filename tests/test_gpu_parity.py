@@ -252,3 +252,21 @@ def test_fast_and_generic_kernels_agree(mp, monkeypatch, dist, p):
                      P_ref=ref[0], I_ref=ref[1], P2=ref[2], label=lab)
     agree = np.mean(I1 == I2)
     assert agree > 0.999, agree
+
+
+@pytest.mark.parametrize("kind,m,dist,seed", [("uniform", 32, "euclid", 91), ("uniform", 48, "znorm", 92),
+                                              ("flat", 64, "znorm", 93)])
+def test_block_filters_are_exact(mp, kind, m, dist, seed):
+    """The block filters only skip blocks whose candidates cannot pass: forced on
+    and off they give the same profile bit for bit.  On i.i.d. uniform data the
+    distances are tightly spread, so the bounds fail often and many blocks are
+    replayed; the flat run gives the z-normalised filter NaN rows and columns."""
+    s = W.small(kind, 230_000, m, seed, dtype=np.float32)
+    Pf, If = run(mp, s.T, s.m, s.excl, dist, variant=mp.MP_VARIANT_FAST_FILTER)
+    Pn, In = run(mp, s.T, s.m, s.excl, dist, variant=mp.MP_VARIANT_FAST)
+    np.testing.assert_array_equal(If, In)
+    np.testing.assert_array_equal(Pf, Pn)
+    rows = np.random.default_rng(seed).choice(s.N, 120, replace=False)
+    ref = oracle.brute_rows(s.T, s.m, s.excl, rows, dist)
+    parity.check(s.T, s.m, s.excl, dist, 2.0, Pf, If, RTOL32, rows=rows, P_ref=ref[0], I_ref=ref[1], P2=ref[2],
+                 label=f"filter {kind} {dist}")
