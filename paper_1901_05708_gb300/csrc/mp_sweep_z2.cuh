@@ -153,6 +153,7 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
     const float THR_OPEN = __int_as_float(0x7f7fffff);  // largest finite float
     const int tag_mask = ~(Z_D - 1);
     const float2 ONE = make_float2(1.f, 1.f);
+    const bool r4 = ZN && m >= 64;  // fast blocks fold the low word every 4th row instead of every 2nd
 
     // ---- anchors in float-float, from the definition: the covariance of (row r_s,
     // diagonal kt + d) (z-norm, stored negated), or the sum of the p-norm terms
@@ -314,9 +315,12 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
         };
         // one covariance step into chunk row ul, partner window offset o
         // The increments go into the low word only; renorm() folds it into the
-        // high word with an error-free Fast2Sum after every second row, so the
-        // low word never holds more than two increments and its rounding stays
-        // at the size of the increments' own rounding.
+        // high word with an error-free Fast2Sum after every second row (every
+        // fourth for z-normalised windows of m >= 64, whose increments are small
+        // against the covariance), so the low word never holds more than a few
+        // increments and its rounding stays at the size of the increments' own
+        // rounding.  Filter and tracked passes fold on the same rows, so a
+        // block's state does not depend on which of them ran.
         auto step = [&](int ul, const float2 *WF, const float2 *WG, int o) {
             const float2 fi = IF[ul], gi = IG[ul];
 #pragma unroll
@@ -432,7 +436,7 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                                 bmb = min3f(bmb, qa.y, qb.y);
                             }
                         }
-                        if ((ul & 1) == 0) renorm();
+                        if ((ul & 1) == 0 && (!r4 || (ul & 3) == 0)) renorm();
                     }
                     if constexpr (ZN) {
                         // the row form rounds differently from the tracked pass's q
@@ -488,7 +492,7 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                     step(ulb + ul1, WF, WG, ul1);
 #pragma unroll
                     for (int d = 0; d < Z_D; ++d) q[d] = score(ZN ? II[ulb + ul1] : ONE, WI[ul1 + d], d);
-                    renorm();
+                    if (!r4 || (pr & 1)) renorm();
                     v2_tag8(t1a, q, false, tag_mask);
                     v2_tag8(t1b, q, true, tag_mask);
                     const float r0a = v2_min8(t0a), r0b = v2_min8(t0b), r1a = v2_min8(t1a), r1b = v2_min8(t1b);
