@@ -40,7 +40,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one sweep launch, from a one-pass ncu capture of the
 # current kernel on the full-size workload (profiles/aamp_n1048576_m256_launches.md);
 # None where no capture of the current kernel exists.
-SWEEP_DRAM_BYTES = {("aamp_1m", 1 << 20): 13_370_880 + 161_536}
+SWEEP_DRAM_BYTES = {("aamp_1m", 1 << 20): 13_370_880 + 161_536, ("acamp_1m", 1 << 20): 33_698_304 + 1_703_680}
 
 
 def peaks():
