@@ -69,7 +69,7 @@ typedef enum {
 typedef enum { MP_DIST_EUCLID = 0, MP_DIST_PNORM = 1, MP_DIST_ZNORM = 2 } mp_dist;
 
 /* Kernel of the FP32 sweep.  Euclidean / p-norm, AUTO: the two-stream kernel
- * where it applies (FP32 input, m a multiple of 32 up to 384, p in {1, 2, 3},
+ * where it applies (FP32 input, m a multiple of 32 up to 416, p in {1, 2, 3},
  * default re-anchor interval), with the block filter for p = 2 and
  * N >= 200,000; else,
  * for m >= 512 and p in {1, 2, 3} with float32 input (or where the generic
