@@ -81,7 +81,15 @@ typedef enum { MP_DIST_EUCLID = 0, MP_DIST_PNORM = 1, MP_DIST_ZNORM = 2 } mp_dis
  * not apply.  The filter only skips candidates that cannot pass, so with or
  * without it the results are the same bit for bit.
  * The others force a choice (MP_ERR_UNSUPPORTED where it does not apply);
- * mp_autotune times them. */
+ * mp_autotune times them (not MP_VARIANT_ZRAW).
+ * MP_VARIANT_ZRAW runs Algorithm 2 as printed (Lemma 3): the dot product
+ * C = sum t_{i+l} t_{j+l} carried along each diagonal and
+ * rho = (C - A_i A_j / m) / sqrt(S_i S_j) with the window sums A, in the
+ * precision of mp_options.precision, re-anchored like the other plain sweeps
+ * (every `reanchor` rows, default 512 in FP32, 256 in FP64).  The numerator
+ * cancels when a window's mean is large against its spread, which the
+ * centred covariance of the other kernels avoids: it exists to measure that
+ * loss and the speed of the paper's form, not for use. */
 typedef enum {
     MP_VARIANT_AUTO = 0,
     MP_VARIANT_FAST_FILTER = 1,  /* two-stream kernel with the block filter (p = 2); */
@@ -89,8 +97,10 @@ typedef enum {
     MP_VARIANT_FAST = 2,         /* two-stream kernel; z-normalised kernel, no filter */
     MP_VARIANT_GENERIC = 3,      /* generic kernel (any p, input type; reanchor;     */
                                  /* shared memory limits m to about 12,000)          */
-    MP_VARIANT_TALL = 4          /* tall-tile kernel: float-float sums, tiles of      */
+    MP_VARIANT_TALL = 4,         /* tall-tile kernel: float-float sums, tiles of      */
                                  /* max(8192, 8m) rows (p in {1, 2, 3}; long windows) */
+    MP_VARIANT_ZRAW = 5          /* ablation, z-normalised only, FP32 or FP64 sweep:  */
+                                 /* Algorithm 2's raw sums (see below)               */
 } mp_variant;
 
 typedef struct mp_options {

@@ -148,7 +148,7 @@ mp_status check_problem(Problem &pb, const void *T, const double *P, const int64
         return fail(MP_ERR_INVALID_ARG, "precision %d", pb.opt.precision);
     if (pb.opt.reanchor < 0) return fail(MP_ERR_INVALID_ARG, "reanchor %d < 0", pb.opt.reanchor);
     if (pb.opt.polish != 0 && pb.opt.polish != 1) return fail(MP_ERR_INVALID_ARG, "polish %d", pb.opt.polish);
-    if (pb.opt.variant < MP_VARIANT_AUTO || pb.opt.variant > MP_VARIANT_TALL)
+    if (pb.opt.variant < MP_VARIANT_AUTO || pb.opt.variant > MP_VARIANT_ZRAW)
         return fail(MP_ERR_INVALID_ARG, "variant %d", pb.opt.variant);
     if (pb.opt.k_begin < 0) return fail(MP_ERR_INVALID_ARG, "k_begin %lld < 0", (long long)pb.opt.k_begin);
     if (!T || !P || !I) return fail(MP_ERR_INVALID_ARG, "NULL T, P or I");
@@ -411,6 +411,8 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
         return fail(MP_ERR_UNSUPPORTED, "the block filter exists for p = 2 and for the z-normalised kernel");
     if (v == MP_VARIANT_GENERIC && (pb.opt.precision != MP_PREC_FP32 || pb.dist == MP_DIST_ZNORM))
         return fail(MP_ERR_UNSUPPORTED, "the generic kernel is the FP32 Euclidean / p-norm sweep");
+    if (v == MP_VARIANT_ZRAW && pb.dist != MP_DIST_ZNORM)
+        return fail(MP_ERR_UNSUPPORTED, "the raw-sum variant is Algorithm 2's, for the z-normalised distance");
     if (v == MP_VARIANT_TALL && !tall_applies(pb))
         return fail(MP_ERR_UNSUPPORTED, "the tall-tile kernel is the FP32 sweep for p in {1, 2, 3}");
     const Layout L = layout(pb);
@@ -464,12 +466,24 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
             cudaError_t e;
             SweepEvents ev(st);
             if (g.tiles > 0) counted();
-            if (pb.dist == MP_DIST_ZNORM && f64) {
+            const bool zraw = pb.opt.variant == MP_VARIANT_ZRAW;
+            if (pb.dist == MP_DIST_ZNORM && f64 && zraw) {
+                mpk::VarF64ZRaw v{x64, reinterpret_cast<const double *>(w + L.mu),
+                                  reinterpret_cast<const double *>(w + L.S),
+                                  reinterpret_cast<const unsigned char *>(w + L.flat), pb.m,
+                                  reinterpret_cast<mpk::Key128 *>(w + L.keys128), err};
+                e = mpk::launch_simple(g, v, pb.opt.reanchor > 0 ? pb.opt.reanchor : 256, st);
+            } else if (pb.dist == MP_DIST_ZNORM && f64) {
                 mpk::VarF64Z v{x64, reinterpret_cast<const double *>(w + L.mu),
                                reinterpret_cast<const double *>(w + L.S),
                                reinterpret_cast<const unsigned char *>(w + L.flat), pb.m,
                                reinterpret_cast<mpk::Key128 *>(w + L.keys128), err};
                 e = mpk::launch_simple(g, v, pb.opt.reanchor > 0 ? pb.opt.reanchor : 256, st);
+            } else if (pb.dist == MP_DIST_ZNORM && zraw) {
+                mpk::VarF32ZRaw v{reinterpret_cast<const float *>(w + L.hi), reinterpret_cast<const float *>(w + L.muf),
+                                  reinterpret_cast<const float *>(w + L.inv), pb.m,
+                                  reinterpret_cast<unsigned long long *>(w + L.keys)};
+                e = mpk::launch_simple(g, v, pb.opt.reanchor > 0 ? pb.opt.reanchor : 512, st);
             } else if (pb.dist == MP_DIST_ZNORM && !getenv_generic()) {
                 mpk::SweepZArgs za{};
                 za.t = reinterpret_cast<const float *>(w + L.hi);

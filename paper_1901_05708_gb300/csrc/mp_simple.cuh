@@ -245,4 +245,74 @@ struct VarF32Z {
     }
 };
 
+// ---- z-normalised, raw sums (Algorithm 2 as printed; an ablation) -------------------
+// The paper's form of Lemma 3: the dot product C_{i,j} = sum_l t_{i+l} t_{j+l}
+// carried with C_{i,j} = C_{i-1,j-1} + t_{i+m-1} t_{j+m-1} - t_{i-1} t_{j-1}, and
+// rho = (C - A_i A_j / m) / sqrt(S_i S_j) with the window sums A = m mu.  The
+// numerator cancels when a window's mean is large against its spread; the
+// centred covariance of VarF64Z / VarF32Z avoids that.  Both precisions take
+// the same denominators and flat rule as the centred variants, so only the
+// form of the sum differs.
+struct VarF64ZRaw {
+    using Real = double;
+    struct State { double c; };
+    const double *x, *mu, *S;
+    const unsigned char *flat;
+    int m;
+    Key128 *keys;
+    int *err;
+    __device__ static double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+    __device__ State anchor(long long i, long long k) const {
+        double acc = 0.0;
+        for (int l = 0; l < m; ++l) acc = fma(x[i + l], x[i + k + l], acc);
+        return State{acc};
+    }
+    __device__ void step(State &s, long long i, long long k) const {
+        const long long a = i - 1, b = i + k - 1;
+        s.c = fma(x[a + m], x[b + m], fma(-x[a], x[b], s.c));
+    }
+    __device__ double score(const State &s, long long i, long long k) const {
+        if (flat[i] || flat[i + k]) return __longlong_as_double(0x7ff8000000000000ll);  // NaN
+        const double num = s.c - static_cast<double>(m) * mu[i] * mu[i + k];
+        const double q = 1.0 - num / sqrt(S[i] * S[i + k]);
+        return q < 0 ? 0.0 : (q > 2.0 ? 2.0 : q);
+    }
+    __device__ void emit(long long target, double val, long long k, int right) const {
+        const double cur = __longlong_as_double(static_cast<long long>(keys[target].hi));
+        if (!(val <= cur) && keys[target].hi != KEY_NONE) return;
+        if (!atomic_min_key128(&keys[target], static_cast<unsigned long long>(__double_as_longlong(val)),
+                               static_cast<unsigned long long>(2 * k + right)))
+            atomicOr(err, ERR_CAS_SPIN);
+    }
+};
+
+struct VarF32ZRaw {
+    using Real = float;
+    struct State { float c; };
+    const float *t;    // FP32 series
+    const float *muf;  // FP32 window means
+    const float *inv;  // 1 / sqrt(S) from the FP64 statistics; NaN for a flat window
+    int m;
+    unsigned long long *keys;
+    __device__ static float inf() { return __int_as_float(0x7f800000); }
+    __device__ State anchor(long long i, long long k) const {
+        float acc = 0.f;
+        for (int l = 0; l < m; ++l) acc = fmaf(t[i + l], t[i + k + l], acc);
+        return State{acc};
+    }
+    __device__ void step(State &s, long long i, long long k) const {
+        const long long a = i - 1, b = i + k - 1;
+        s.c = fmaf(t[a + m], t[b + m], fmaf(-t[a], t[b], s.c));
+    }
+    __device__ float score(const State &s, long long i, long long k) const {
+        const float num = fmaf(-static_cast<float>(m) * muf[i], muf[i + k], s.c);
+        const float q = fmaf(-num, inv[i] * inv[i + k], 1.0f);  // NaN if flat
+        return q < 0.f ? 0.f : q;
+    }
+    __device__ void emit(long long target, float val, long long k, int right) const {
+        if (!(val < __int_as_float(0x7f800000))) return;
+        atomicMin(&keys[target], make_key(__float_as_uint(val), k, right));
+    }
+};
+
 }  // namespace mpk

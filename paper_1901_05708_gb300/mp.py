@@ -29,7 +29,8 @@ MP_OK, MP_ERR_INVALID_ARG, MP_ERR_UNSUPPORTED, MP_ERR_WORKSPACE, MP_ERR_CUDA, MP
 MP_F32, MP_F64 = 0, 1
 MP_PREC_FP32, MP_PREC_FP64 = 0, 1
 MP_DIST_EUCLID, MP_DIST_PNORM, MP_DIST_ZNORM = 0, 1, 2
-MP_VARIANT_AUTO, MP_VARIANT_FAST_FILTER, MP_VARIANT_FAST, MP_VARIANT_GENERIC, MP_VARIANT_TALL = 0, 1, 2, 3, 4
+MP_VARIANT_AUTO, MP_VARIANT_FAST_FILTER, MP_VARIANT_FAST, MP_VARIANT_GENERIC, MP_VARIANT_TALL, MP_VARIANT_ZRAW = \
+    0, 1, 2, 3, 4, 5
 
 EXPORTS = ("mp_options_default", "mp_workspace_size", "mp_aamp", "mp_pnorm", "mp_acamp",
            "mp_sync_status", "mp_last_error", "mp_status_string", "mp_version", "mp_launch_count",

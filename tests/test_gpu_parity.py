@@ -270,3 +270,23 @@ def test_block_filters_are_exact(mp, kind, m, dist, seed):
     ref = oracle.brute_rows(s.T, s.m, s.excl, rows, dist)
     parity.check(s.T, s.m, s.excl, dist, 2.0, Pf, If, RTOL32, rows=rows, P_ref=ref[0], I_ref=ref[1], P2=ref[2],
                  label=f"filter {kind} {dist}")
+
+
+def test_raw_sum_ablation(mp):
+    """MP_VARIANT_ZRAW, Algorithm 2's raw-sum form: in FP64 it meets the FP64
+    bar on a stationary series (mean small against the spread, so the
+    numerator C - A_i A_j / m barely cancels); in FP32 it returns exact
+    distances (polished) at valid neighbours close to the best; it exists only
+    for the z-normalised distance."""
+    s = W.small("uniform", 3000, 32, 95, dtype=np.float32)
+    ref = oracle.brute_rows(s.T, s.m, s.excl, np.arange(s.N), "znorm")
+    P, I = run(mp, s.T, s.m, s.excl, "znorm", precision="fp64", variant=mp.MP_VARIANT_ZRAW)
+    parity.check(s.T, s.m, s.excl, "znorm", 2.0, P, I, RTOL64, P_ref=ref[0], I_ref=ref[1], P2=ref[2],
+                 label="raw sums fp64")
+    P, I = run(mp, s.T, s.m, s.excl, "znorm", variant=mp.MP_VARIANT_ZRAW)
+    assert np.all(np.abs(I - np.arange(s.N)) > s.excl)
+    d = oracle.pair_dist(s.T.astype(np.float64), s.m, np.arange(s.N), I, "znorm", 2.0)
+    np.testing.assert_allclose(P, d, rtol=1e-12)
+    assert np.all(P <= ref[0] * (1 + 1e-3))
+    with pytest.raises(mp.MPError):
+        run(mp, s.T, s.m, s.excl, "euclid", variant=mp.MP_VARIANT_ZRAW)
