@@ -148,7 +148,28 @@ def oracle_sample(series: W.Series, target_s: float = 12.0):
     cells = sum(series.N - k for k in range(k0, k0 + K))
     return {"value": cells / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{series.name}: diagonals {k0}..{k0 + K - 1} ({cells:.3e} cells) in {dt:.2f} s",
-            "seconds": dt, "cells": cells}
+            "cpu": cpu_model(), "seconds": dt, "cells": cells}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
 
 
 def run_reference(args):
@@ -176,7 +197,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": dict(config, precision="fp64 CPU oracle (OpenMP over diagonals)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": runs[0]["cores"], "kind": "oracle",
-                             "sample": runs[0]["sample"]},
+                             "sample": runs[0]["sample"], "cpu": runs[0]["cpu"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -200,6 +221,18 @@ for _lg in (8, 10, 12, 14, 16):
         (lambda lg: lambda seed, n: W.Series(f"uniform_n262144_m{1 << lg}", W.uniform(1 << 18, seed + 4), 1 << lg,
                                              W.excl_zone(1 << lg), W.EUCLID))(_lg),
         f"AAMP pure Euclidean, i.i.d. uniform values, n = 2^18, m = 2^{_lg}", 4)
+
+
+# the paper's other timing shape (Sec. 5.1): i.i.d. uniform series, m = 2^8, n from 2^14 to 2^20, both distances
+for _lg in range(14, 21):
+    WORKLOADS[f"s1_aamp_n{1 << _lg}"] = (
+        (lambda lg: lambda seed, n: W.Series(f"uniform_n{1 << lg}_m256", W.uniform(1 << lg, seed + 4), 256,
+                                             W.excl_zone(256), W.EUCLID))(_lg),
+        f"AAMP pure Euclidean, i.i.d. uniform values, n = 2^{_lg}, m = 256", 4)
+    WORKLOADS[f"s1_acamp_n{1 << _lg}"] = (
+        (lambda lg: lambda seed, n: W.Series(f"uniform_n{1 << lg}_m256", W.uniform(1 << lg, seed + 4), 256,
+                                             W.excl_zone(256), W.ZNORM))(_lg),
+        f"ACAMP z-normalised, i.i.d. uniform values, n = 2^{_lg}, m = 256", 4)
 
 
 def workload_config(series: W.Series, desc: str = WORKLOADS["aamp_1m"][1], precision: str = "fp32") -> dict:
@@ -301,7 +334,7 @@ def bench_batch(args, torch, mp, lib, dev, stream, rank, ws):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         longest = max(b.series, key=lambda x: x.n)
         cb = oracle_sample(longest, target_s=args.ref_seconds)
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu")}
     elif rank == 0:
         line["cpu_baseline"] = None
     plan.close()
@@ -467,6 +500,11 @@ def main():
                 "acamp_1m": "the series, the FP32 operands (df, dg, inv, float-float means) and the keys once, ~32 MB"}
         roof["traffic_note"] = ("bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum); "
                                 "algorithmic: " + algo[args.workload])
+    if series.dist == W.EUCLID and series.p == 2.0:
+        # the FLOP convention: 6 flops per cell (2 FADD, 2 FMUL, 2 FADD for s += e^2 - f^2) against
+        # 2 flops per lane per cycle; its ceiling is 6 / (2 x 4) = 0.75 by construction
+        roof["flop_convention"] = {"flops_per_cell": 6, "ceiling": 0.75,
+                                   "frac": achieved * 6 / (sms * FP32_LANES_PER_SM * 2 * f_max / 1e9)}
     if clk.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (sms * FP32_LANES_PER_SM * clk["sm_mhz"] * 1e6
                                                      / instr_per_cell / 1e9)
@@ -486,7 +524,7 @@ def main():
         line["fp64_sweep"] = fp64
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and series.dist == W.EUCLID:
         cb = oracle_sample(series, target_s=args.ref_seconds)
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu")}
     elif rank == 0:
         line["cpu_baseline"] = None  # the CPU baseline is timed on the default Euclidean workload
     if rank == 0:
