@@ -160,6 +160,10 @@ def load(path: str | None = None):
 
 def options(precision: str = "fp32", reanchor: int = 0, polish: bool = True,
             k_range: tuple[int, int] | None = None, variant: int = MP_VARIANT_AUTO) -> Options:
+    """mp_options for the calls below.  variant (include/mp.h, mp_variant): MP_VARIANT_AUTO;
+    MP_VARIANT_FAST_FILTER / MP_VARIANT_FAST: the two-stream kernel with / without its block
+    filter (the z-normalised kernel with / without its filter for acamp); MP_VARIANT_GENERIC;
+    MP_VARIANT_TALL; MP_VARIANT_ZRAW: Algorithm 2's raw-sum form, an ablation (acamp only)."""
     o = Options()
     load().mp_options_default(ctypes.byref(o))
     o.precision = {"fp32": MP_PREC_FP32, "fp64": MP_PREC_FP64}[precision]
