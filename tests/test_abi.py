@@ -81,6 +81,15 @@ def test_argument_checks_need_no_gpu(lib):
     lib.mp_options_default(ctypes.byref(o))
     o.precision = 9
     assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG
+    lib.mp_options_default(ctypes.byref(o))
+    o.variant = mp.MP_VARIANT_ZRAW + 1
+    assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG             # no such variant
+    o.variant = mp.MP_VARIANT_ZRAW
+    assert _call_aamp(lib, opt=o) == E.MP_ERR_UNSUPPORTED             # the raw-sum form is Algorithm 2's
+    o.variant = mp.MP_VARIANT_GENERIC                                   # the z-normalised distance has no generic kernel
+    vp = ctypes.c_void_p
+    assert lib.mp_acamp(vp(0x1000), 0, 100, 10, 2, vp(0x2000), vp(0x3000), vp(0x10000), 1 << 30,
+                        ctypes.byref(o), vp(0)) == E.MP_ERR_UNSUPPORTED
     vp = ctypes.c_void_p
     assert lib.mp_pnorm(vp(0x1000), 0, 100, 10, 2, 0.5, vp(0x2000), vp(0x3000), vp(0x10000), 1 << 30,
                         None, vp(0)) == E.MP_ERR_INVALID_ARG
