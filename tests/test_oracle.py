@@ -364,6 +364,62 @@ def test_rows_polish_and_runner_up(oracle_mod):
     np.testing.assert_allclose(oracle_mod.polish(s.T, 24, Iz, "znorm"), Pz, rtol=1e-8)
 
 
+def runner_up_from_matrix(D, excl, I):
+    """Second-best score of each row from an all-pairs matrix: the minimum over
+    candidates j of row x (|j - x| > excl) that also lie outside the winner's
+    exclusion zone (|j - I[x]| > excl); +inf if there is none."""
+    N = D.shape[0]
+    P2 = np.full(N, np.inf)
+    j = np.arange(N)
+    for x in range(N):
+        if I[x] < 0:
+            continue
+        ok = (np.abs(j - x) > excl) & (np.abs(j - I[x]) > excl) & np.isfinite(D[x])
+        if ok.any():
+            P2[x] = D[x, ok].min()
+    return P2
+
+
+@pytest.mark.parametrize("seed", range(5))
+@pytest.mark.parametrize("dist,p", [("euclid", 2.0), ("pnorm", 1.0), ("pnorm", 3.0), ("znorm", 2.0)])
+def test_runner_up_matches_scipy(oracle_mod, seed, dist, p):
+    """orc_brute_rows' runner-up P2 (which decides where the GPU's index must
+    equal the oracle's) against the same quantity taken from scipy's all-pairs
+    matrix: every row of tiny series, excl in {0, 1, m/4}.  Cases where the
+    winner's zone straddles the row's own zone occur on every series (the
+    winner sits just outside the row's zone); a planted copy next to the row's
+    zone forces one for excl = m/4."""
+    rng = np.random.default_rng(900 + seed)
+    m = int(rng.integers(4, 10))
+    n = int(rng.integers(3 * m, 60))
+    T = np.cumsum(rng.standard_normal(n))
+    # a near-copy of window 5 placed so that its start is just outside the zone
+    # of row 5 for excl = m // 4, whose own zone then overlaps row 5's
+    c = 5 + m // 4 + 1
+    if c + m <= n and 5 + m <= n:
+        T[c:c + m] = T[5:5 + m] + 0.02 * rng.standard_normal(m)
+    D = library_matrix(T, m, dist, p)
+    N = n - m + 1
+    rows = np.arange(N)
+    for excl in sorted({0, 1, max(1, m // 4)}):
+        Pl, Il = profile_from_matrix(D, excl)
+        P2l = runner_up_from_matrix(D, excl, Il)
+        Pr, Ir, P2r = oracle_mod.brute_rows(T, m, excl, rows, dist, p, raw=True)
+        np.testing.assert_array_equal(Ir, Il)
+        np.testing.assert_allclose(Pr, Pl, rtol=1e-12, atol=1e-12)
+        fin = np.isfinite(P2l)
+        assert np.array_equal(np.isfinite(P2r), fin), f"excl={excl}: runner-up exists in a different set of rows"
+        np.testing.assert_allclose(P2r[fin], P2l[fin], rtol=1e-12, atol=1e-12,
+                                   err_msg=f"{dist} p={p} excl={excl}")
+        # the distance form (the final root) of the same runner-up
+        _, _, P2d = oracle_mod.brute_rows(T, m, excl, rows, dist, p, raw=False)
+        np.testing.assert_allclose(P2d[fin], finish(P2l[fin], dist, p), rtol=1e-11, atol=1e-7)
+        # straddling zones: some winner lies within 2 excl of its row, so the
+        # zones around the row and around the winner overlap
+        if excl == max(1, m // 4):
+            assert np.any((Il >= 0) & (np.abs(Il - rows) <= 2 * excl)), "no straddling case exercised"
+
+
 def test_diagonal_ranges_merge(oracle_mod):
     """Disjoint diagonal ranges merged by (score, 2k + side) give the full
     profile: the rule the multi-rank merge relies on."""

@@ -66,3 +66,23 @@ def test_tie_inside_winner_zone_passes():
     Pfull[rows], Ifull[rows] = Pg, Ig
     parity.check(T, s.m, s.excl, "pnorm", 1.0, Pfull, Ifull, 1e-5, rows=rows, P_ref=P, I_ref=I, P2=P2,
                  label="tie")
+
+
+def test_znorm_strict_unless_raw_fp32():
+    """The z-normalised rules are the contract's (1e-5 relative, rtol sqrt(m)
+    floor): a P off by more than that fails, unless the check is explicitly of
+    the FP32 kernel's raw sweep value (raw_z32), whose stated q resolution
+    widens rule (i) only."""
+    s = W.small("walk", 900, 16, 8)
+    T = s.T.copy()
+    T[600:616] = T[100:116] + 1e-4 * np.random.default_rng(3).standard_normal(16)  # a near-identical pair
+    P, I = oracle.brute(T, s.m, s.excl, "znorm")
+    Pg = P.copy()
+    x = int(np.argmin(P))
+    tol = 1e-5 * P[x] + 1e-5 * np.sqrt(s.m)
+    loose = np.sqrt(P[x] ** 2 + 2 * s.m * parity.Q_ATOL_Z32) - P[x]
+    assert loose > 2 * tol
+    Pg[x] = P[x] + tol + 0.5 * loose
+    with pytest.raises(AssertionError):
+        parity.check(T, s.m, s.excl, "znorm", 2.0, Pg, I, 1e-5, label="polished")
+    parity.check(T, s.m, s.excl, "znorm", 2.0, Pg, I, 1e-5, label="raw", raw_z32=True)
