@@ -37,10 +37,42 @@ METRIC = "distance-matrix cells/s (GCells/s) at 1 GB300 + % FP32 roofline, FP32 
 UNIT = "GCells/s"
 FP32_INSTR_PER_CELL = 4          # minimum FP32-pipe instructions per cell (Lemma 1 update)
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) of one sweep launch, from a one-pass ncu capture of the
-# current kernel on the full-size workload (profiles/aamp_n1048576_m256_launches.md);
-# None where no capture of the current kernel exists.
-SWEEP_DRAM_BYTES = {("aamp_1m", 1 << 20): 13_370_880 + 161_536, ("acamp_1m", 1 << 20): 33_698_304 + 1_703_680}
+CSRC = os.path.join(ROOT, "paper_1901_05708_gb300", "csrc")
+# the sources that make up each workload's sweep kernel (their hash names the kernel version)
+SWEEP_SOURCES = {
+    "euclid": ["mp_device.cuh", "mp_sweep2.cuh", "k_sweep2.cu"],
+    "pnorm": ["mp_device.cuh", "mp_sweep2.cuh", "k_sweep2_p13.cu"],
+    "znorm": ["mp_device.cuh", "mp_sweep2.cuh", "mp_sweep_z2.cuh", "k_sweepz.cu"],
+}
+
+
+def kernel_version(dist_name: str) -> str:
+    """Hash of the sources of the sweep kernel a workload runs."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in SWEEP_SOURCES[dist_name]:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def sweep_dram_bytes(workload: str, n: int, version: str):
+    """DRAM bytes (read + write) of one sweep launch from the committed ncu
+    summaries under profiles/: a line
+      dram_bytes_per_launch: workload=<name> n=<n> kernel=<version> bytes=<B>
+    recorded for this workload, size and kernel version; None when the kernel
+    has changed since its last capture."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            for line in f:
+                line = line.strip().strip("`")
+                if not line.startswith("dram_bytes_per_launch:"):
+                    continue
+                kv = dict(x.split("=", 1) for x in line.split(":", 1)[1].split())
+                if kv.get("workload") == workload and int(kv.get("n", -1)) == n and kv.get("kernel") == version:
+                    return int(kv["bytes"])
+    return None
 
 
 def peaks():
@@ -366,6 +398,9 @@ def main():
     from paper_1901_05708_gb300 import mp
 
     ws, rank, local = dist_env()
+    if args.gpus != ws:
+        raise SystemExit(f"--gpus {args.gpus} but {ws} ranks: launch N > 1 with torch.distributed.run "
+                         f"--nproc-per-node N (one rank per GPU)")
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
@@ -489,17 +524,20 @@ def main():
     peak_cells = sms * FP32_LANES_PER_SM * f_max / instr_per_cell / 1e9
     sweep_avg_ms = float(np.mean(sweep_ms))
     achieved = cells / (sweep_avg_ms * 1e-3) / 1e9
-    traffic = None if args.k_range else SWEEP_DRAM_BYTES.get((args.workload, args.n))
+    version = kernel_version(dname)
+    traffic = None if args.k_range else sweep_dram_bytes(args.workload, args.n, version)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_cells, "unit": UNIT,
             "frac": achieved / peak_cells, "traffic": traffic,
             "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {f_max/1e6:.0f} MHz "
                            f"({src} sm_max_mhz) / {instr_per_cell} FP32 instructions per cell",
-            "kernel": "diagonal sweep (a3-a5)", "kernel_ms": sweep_avg_ms}
+            "kernel": "diagonal sweep (a3-a5)", "kernel_ms": sweep_avg_ms, "kernel_version": version}
     if traffic is not None:
-        algo = {"aamp_1m": "the series and the keys once, ~12.6 MB",
-                "acamp_1m": "the series, the FP32 operands (df, dg, inv, float-float means) and the keys once, ~32 MB"}
-        roof["traffic_note"] = ("bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum); "
-                                "algorithmic: " + algo[args.workload])
+        algo = {"euclid": "the series and the keys once: 4n + 8N bytes",
+                "pnorm": "the series and the keys once: 4n + 8N bytes",
+                "znorm": "the series, the FP32 operands (df, dg, inv, float-float means) and the keys once: "
+                         "4n + 28N bytes"}
+        roof["traffic_note"] = ("bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum) of this "
+                                "kernel version; algorithmic: " + algo[dname])
     if series.dist == W.EUCLID and series.p == 2.0:
         # the FLOP convention: 6 flops per cell (2 FADD, 2 FMUL, 2 FADD for s += e^2 - f^2) against
         # 2 flops per lane per cycle; its ceiling is 6 / (2 x 4) = 0.75 by construction
@@ -522,11 +560,11 @@ def main():
     if fp64 is not None:
         fp64["fp32_over_fp64"] = achieved / fp64["value"]
         line["fp64_sweep"] = fp64
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline and series.dist == W.EUCLID:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = oracle_sample(series, target_s=args.ref_seconds)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu")}
     elif rank == 0:
-        line["cpu_baseline"] = None  # the CPU baseline is timed on the default Euclidean workload
+        line["cpu_baseline"] = None  # timed on rank 0 at N = 1 only
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -198,9 +198,10 @@ mp_status mp_set_sweep_events(void *ev_start, void *ev_end);
  *  - Problems whose workspace (mp_workspace_size(MP_DIST_EUCLID, ...)) is
  *    larger than the scratch are rejected with MP_ERR_UNSUPPORTED; with
  *    float32 input that is n up to about 1.6 million samples.
- *  - The first call on each device looks up the scratch address on that
- *    device (the device must be current); make that first call before any
- *    CUDA stream capture.
+ *  - Every call looks up the scratch address on the current device (a
+ *    host-side query, after the argument checks); the first lookup on a
+ *    device may load the library's device code there, so make the first
+ *    call on each device before any CUDA stream capture.
  *  - All calls on a device share the one scratch array, which keeps the
  *    contents of the last call (every call initialises what it reads).
  *    Calls that overlap on the GPU -- on different streams, or from

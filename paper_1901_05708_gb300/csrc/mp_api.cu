@@ -21,11 +21,9 @@
 #include <nvtx3/nvToolsExt.h>
 #include "mp_device.cuh"
 #include "mp_prep.cuh"
-#include "mp_sweep.cuh"
-#include "mp_sweep2.cuh"
-#include "mp_sweep_z2.cuh"
+#include "mp_kernels.h"
 #include "mp_launch.cuh"
-#include "mp_batch.cuh"
+#include "mp_batch_prep.cuh"
 #include "mp_stream.cuh"
 
 namespace {
@@ -214,18 +212,6 @@ mp_status prep_series(const Problem &pb, const Layout &L, const void *T, char *w
     return MP_OK;
 }
 
-template <int KIND, bool SPLIT>
-mp_status launch_sweep_t(const mpk::SweepArgs &a, size_t smem, cudaStream_t st) {
-    auto kern = mpk::sweep_kernel<KIND, SPLIT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(sweep)");
-    {
-        SweepEvents ev(st);
-        kern<<<static_cast<unsigned>(a.tiles), mpk::SW_NT, smem, st>>>(a);
-    }
-    counted();
-    return MP_OK;
-}
 
 // Exponent kind of a Euclidean / p-norm problem.
 int kind_of(int dist, double p) {
@@ -247,15 +233,9 @@ bool fast_path_ok(const Problem &pb) {
     return fast_path_applies(pb) && !getenv_generic();
 }
 
-template <int KIND, bool FILTER>
-mp_status launch_sweep2_t(const mpk::Sweep2Args &a, size_t smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(mpk::sweep2_kernel<KIND, FILTER>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(sweep2)");
-    {
-        SweepEvents ev(st);
-        mpk::sweep2_kernel<KIND, FILTER><<<static_cast<unsigned>(a.tiles), mpk::V2_NT, smem, st>>>(a);
-    }
+// Status of a sweep launcher's result, counting the launch.
+mp_status launched(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) return cuda_fail(e, what);
     counted();
     return MP_OK;
 }
@@ -282,30 +262,12 @@ mp_status run_sweep2(const Problem &pb, const Layout &L, char *ws, cudaStream_t 
     if (a.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", a.tiles);
     if (a.tiles <= 0) return MP_OK;
     const size_t smem = mpk::sweep2_smem_bytes(a.m, a.Q);
-    switch (kind_of(pb.dist, pb.p)) {
-        case mpk::K_P1: return launch_sweep2_t<mpk::K_P1, false>(a, smem, st);
-        case mpk::K_P3: return launch_sweep2_t<mpk::K_P3, false>(a, smem, st);
-        default: {
-            const bool filter = pb.opt.variant == MP_VARIANT_FAST_FILTER ||
-                                (pb.opt.variant == MP_VARIANT_AUTO && pb.N >= FILTER_MIN_N);
-            return filter ? launch_sweep2_t<mpk::K_P2, true>(a, smem, st)
-                          : launch_sweep2_t<mpk::K_P2, false>(a, smem, st);
-        }
-    }
-}
-
-template <int KIND, bool FILTER>
-mp_status launch_tall_t(const mpk::SweepZArgs &a, cudaStream_t st) {
-    const size_t smem = mpk::sweepz_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(mpk::sweepz_kernel<KIND, FILTER>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tall sweep)");
-    {
-        SweepEvents ev(st);
-        mpk::sweepz_kernel<KIND, FILTER><<<static_cast<unsigned>(a.tiles), mpk::Z_NT, smem, st>>>(a);
-    }
-    counted();
-    return cudaGetLastError() == cudaSuccess ? MP_OK : cuda_fail(cudaGetLastError(), "tall sweep launch");
+    const int kind = kind_of(pb.dist, pb.p);
+    SweepEvents ev(st);
+    if (kind != mpk::K_P2) return launched(mpk::sweep2_p13_launch(kind, a, smem, st), "two-stream sweep launch");
+    const bool filter = pb.opt.variant == MP_VARIANT_FAST_FILTER ||
+                        (pb.opt.variant == MP_VARIANT_AUTO && pb.N >= FILTER_MIN_N);
+    return launched(mpk::sweep2_p2_launch(filter, a, smem, st), "two-stream sweep launch");
 }
 
 // Tall-tile Euclidean / p-norm sweep (float-float sums, tiles of max(8192, 8m) rows).
@@ -324,12 +286,10 @@ mp_status run_tall(const Problem &pb, const Layout &L, char *ws, cudaStream_t st
     a.tiles = mpk::z_prefix(a.L, a.nb, a.S);
     if (a.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", a.tiles);
     if (a.tiles <= 0) return MP_OK;
-    switch (kind_of(pb.dist, pb.p)) {
-        case mpk::K_P1: return launch_tall_t<mpk::K_P1, false>(a, st);
-        case mpk::K_P3: return launch_tall_t<mpk::K_P3, false>(a, st);
-        default:
-            return pb.N >= FILTER_MIN_N ? launch_tall_t<mpk::K_P2, true>(a, st) : launch_tall_t<mpk::K_P2, false>(a, st);
-    }
+    const int kind = kind_of(pb.dist, pb.p);
+    SweepEvents ev(st);
+    return launched(mpk::sweepz_launch(kind, kind == mpk::K_P2 && pb.N >= FILTER_MIN_N, a, mpk::sweepz_smem_bytes(), st),
+                    "tall sweep launch");
 }
 
 // The generic kernel's shared memory for this problem (0 if it cannot hold m).
@@ -383,21 +343,13 @@ mp_status run_sweep_f32(const Problem &pb, const Layout &L, char *ws, cudaStream
     const bool split = a.lo != nullptr;
     const size_t smem = mpk::sweep_smem_bytes(a.R, a.m, a.Q, split);
     if (smem > 227 * 1024) return fail(MP_ERR_UNSUPPORTED, "m = %d needs %zu bytes of shared memory", pb.m, smem);
-    const int kind = kind_of(pb.dist, pb.p);
-    switch (kind * 2 + (split ? 1 : 0)) {
-        case 0: return launch_sweep_t<mpk::K_P2, false>(a, smem, st);
-        case 1: return launch_sweep_t<mpk::K_P2, true>(a, smem, st);
-        case 2: return launch_sweep_t<mpk::K_P1, false>(a, smem, st);
-        case 3: return launch_sweep_t<mpk::K_P1, true>(a, smem, st);
-        case 4: return launch_sweep_t<mpk::K_P3, false>(a, smem, st);
-        case 5: return launch_sweep_t<mpk::K_P3, true>(a, smem, st);
-        case 6: return launch_sweep_t<mpk::K_PG, false>(a, smem, st);
-        default: return launch_sweep_t<mpk::K_PG, true>(a, smem, st);
-    }
+    SweepEvents ev(st);
+    return launched(mpk::generic_launch(kind_of(pb.dist, pb.p), split, a, smem, st), "generic sweep launch");
 }
 
-mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_t ws_bytes,
-              const mp_options *opt, void *stream) {
+// Every check of a one-series call that does not involve the workspace:
+// check_problem, then whether the chosen kernel variant applies.
+mp_status check_call(Problem &pb, const void *T, const double *P, const int64_t *I, const mp_options *opt) {
     mp_status s = check_problem(pb, T, P, I, opt);
     if (s != MP_OK) return s;
     const int v = pb.opt.variant;
@@ -415,6 +367,13 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
         return fail(MP_ERR_UNSUPPORTED, "the raw-sum variant is Algorithm 2's, for the z-normalised distance");
     if (v == MP_VARIANT_TALL && !tall_applies(pb))
         return fail(MP_ERR_UNSUPPORTED, "the tall-tile kernel is the FP32 sweep for p in {1, 2, 3}");
+    return MP_OK;
+}
+
+mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_t ws_bytes,
+              const mp_options *opt, void *stream) {
+    mp_status s = check_call(pb, T, P, I, opt);
+    if (s != MP_OK) return s;
     const Layout L = layout(pb);
     if (!ws) return fail(MP_ERR_WORKSPACE, "workspace is NULL (need %zu bytes)", L.total);
     if (!aligned(ws, ALIGN)) return fail(MP_ERR_INVALID_ARG, "workspace not 256-byte aligned");
@@ -504,15 +463,10 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
                 za.S = mpk::z_rows_per_tile(pb.m);
                 za.tiles = mpk::z_prefix(za.L, za.nb, za.S);
                 if (za.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", za.tiles);
-                const size_t smem = mpk::sweepz_smem_bytes();
                 const bool filter = pb.opt.variant == MP_VARIANT_FAST_FILTER ||
                                     (pb.opt.variant == MP_VARIANT_AUTO && pb.N >= FILTER_MIN_N);
-                auto kern = filter ? mpk::sweepz_kernel<mpk::K_Z, true> : mpk::sweepz_kernel<mpk::K_Z, false>;
-                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (e == cudaSuccess && za.tiles > 0) {
-                    kern<<<static_cast<unsigned>(za.tiles), mpk::Z_NT, smem, st>>>(za);
-                    e = cudaGetLastError();
-                }
+                e = za.tiles > 0 ? mpk::sweepz_launch(mpk::K_Z, filter, za, mpk::sweepz_smem_bytes(), st)
+                                 : cudaSuccess;
             } else if (pb.dist == MP_DIST_ZNORM) {
                 mpk::VarF32Z v{reinterpret_cast<const float *>(w + L.hi), reinterpret_cast<const float *>(w + L.muf),
                                reinterpret_cast<const float *>(w + L.df), reinterpret_cast<const float *>(w + L.dg),
@@ -556,28 +510,17 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
 // ---- scratch of mp_aamp_noalloc ------------------------------------------------------
 // Static device memory: loaded with the module on every device that uses the
 // library, never allocated or freed by a call.  Host code must not take its
-// address directly (the host symbol is only a stand-in); the device address
-// is looked up once per device with cudaGetSymbolAddress.
+// address directly (the host symbol is only a stand-in); every call looks the
+// device address up on the current device with cudaGetSymbolAddress (a host-side
+// query), so no address outlives a device reset or a new primary context.
 static __device__ __align__(256) unsigned char mp_noalloc_scratch[MP_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-constexpr int NOALLOC_MAX_DEVICES = 64;
-std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
-
 mp_status noalloc_scratch(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(MP_ERR_UNSUPPORTED, "device %d", dev);
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, mp_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-        g_noalloc_ptr[dev] = p;
-    }
-    *out = g_noalloc_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, mp_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    *out = p;
     return MP_OK;
 }
 }  // namespace
@@ -653,13 +596,6 @@ mp_status mp_acamp(const void *T, int dtype, int64_t n, int32_t m, int64_t excl,
 mp_status mp_aamp_noalloc(const void *T, int dtype, int64_t n, int32_t m, int64_t excl, double *P, int64_t *I,
                           const mp_options *opt, void *stream) {
     g_err[0] = 0;
-    const size_t need = mp_workspace_size(MP_DIST_EUCLID, dtype, n, m, opt);
-    if (need > MP_NOALLOC_SCRATCH_BYTES)
-        return fail(MP_ERR_UNSUPPORTED, "n = %lld needs %zu bytes of scratch; mp_aamp_noalloc has %u",
-                    static_cast<long long>(n), need, MP_NOALLOC_SCRATCH_BYTES);
-    void *ws = nullptr;
-    mp_status st = noalloc_scratch(&ws);
-    if (st != MP_OK) return st;
     Problem pb{};
     pb.dist = MP_DIST_EUCLID;
     pb.dtype = dtype;
@@ -667,20 +603,45 @@ mp_status mp_aamp_noalloc(const void *T, int dtype, int64_t n, int32_t m, int64_
     pb.m = m;
     pb.excl = excl;
     pb.p = 2.0;
-    return run(pb, T, P, I, ws, MP_NOALLOC_SCRATCH_BYTES, opt, stream);
+    // the checks and errors of mp_aamp first, before any CUDA call
+    mp_status st = check_call(pb, T, P, I, opt);
+    if (st != MP_OK) return st;
+    const size_t need = layout(pb).total;
+    if (need > MP_NOALLOC_SCRATCH_BYTES)
+        return fail(MP_ERR_UNSUPPORTED, "n = %lld needs %zu bytes of scratch; mp_aamp_noalloc has %u",
+                    static_cast<long long>(n), need, MP_NOALLOC_SCRATCH_BYTES);
+    void *ws = nullptr;
+    st = noalloc_scratch(&ws);
+    if (st != MP_OK) return st;
+    Problem pr{};
+    pr.dist = MP_DIST_EUCLID;
+    pr.dtype = dtype;
+    pr.n = n;
+    pr.m = m;
+    pr.excl = excl;
+    pr.p = 2.0;
+    return run(pr, T, P, I, ws, MP_NOALLOC_SCRATCH_BYTES, opt, stream);
 }
 
 mp_status mp_sync_status(void *stream) {
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-    int err = 0;
-    e = cudaMemcpyFromSymbol(&err, mp_device_error, sizeof(int));
-    if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
-    if (err) {
-        const int zero = 0;
-        cudaMemcpyToSymbol(mp_device_error, &zero, sizeof(int));
-        return fail(MP_ERR_INTERNAL, "device-side check failed (bits 0x%x)", err);
+    // the error word of every translation unit that holds kernels
+    int *words[] = {mpk::device_error_ptr(), mpk::sweep2_p2_error_word(), mpk::sweep2_p13_error_word(),
+                    mpk::sweepz_error_word(), mpk::batch2_error_word(), mpk::generic_error_word()};
+    int bits = 0;
+    for (int *w : words) {
+        if (!w) return fail(MP_ERR_CUDA, "device error word not found");
+        int v = 0;
+        e = cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+        if (v) {
+            bits |= v;
+            e = cudaMemset(w, 0, sizeof(int));
+            if (e != cudaSuccess) return cuda_fail(e, "clearing the device error word");
+        }
     }
+    if (bits) return fail(MP_ERR_INTERNAL, "device-side check failed (bits 0x%x)", bits);
     return MP_OK;
 }
 
@@ -815,54 +776,24 @@ mp_status batch_validate(const mp_batch_desc *d, const mp_options *opt, mp_optio
     return MP_OK;
 }
 
-template <typename K>
-void batch_grid(mp_batch_plan *pl, int q, K kernel, int nt, int sms) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nt, pl->smem[q]) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
+// Persistent grid of queue qi: as many CTAs as fit on the device at once (per_sm
+// from the occupancy query), at most one per tile.
+void batch_grid(mp_batch_plan *pl, int q, int per_sm, int sms) {
+    if (per_sm < 1) per_sm = 1;
     const long long want = static_cast<long long>(per_sm) * sms;
     pl->grid[q] = static_cast<int>(std::min<long long>(want, static_cast<long long>(pl->tiles[q].size())));
 }
 
-template <int KIND>
-cudaError_t launch_gen_batch(const mp_batch_plan *pl, const mpk::BatchData &bd, const mpk::BatchQueue &q, int qi,
-                             cudaStream_t st) {
-    mpk::sweep_batch_kernel<KIND><<<pl->grid[qi], mpk::SW_NT, pl->smem[qi], st>>>(bd, q, mpk::device_error_ptr());
-    return cudaGetLastError();
-}
-
-template <int KIND, bool FILTER>
-cudaError_t fast_batch_attr(mp_batch_plan *pl, int qi, int sms) {
-    cudaError_t e = cudaFuncSetAttribute(mpk::sweep2_batch_kernel<KIND, FILTER>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(pl->smem[qi]));
-    if (e == cudaSuccess) batch_grid(pl, qi, mpk::sweep2_batch_kernel<KIND, FILTER>, mpk::V2_NT, sms);
-    return e;
-}
-
-template <int KIND>
-cudaError_t gen_batch_attr(mp_batch_plan *pl, int qi, int sms) {
-    cudaError_t e = cudaFuncSetAttribute(mpk::sweep_batch_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(pl->smem[qi]));
-    if (e == cudaSuccess) batch_grid(pl, qi, mpk::sweep_batch_kernel<KIND>, mpk::SW_NT, sms);
-    return e;
-}
-
-cudaError_t gen_dispatch_attr(mp_batch_plan *pl, int qi, int kind, int sms) {
-    switch (kind) {
-        case mpk::K_P1: return gen_batch_attr<mpk::K_P1>(pl, qi, sms);
-        case mpk::K_P3: return gen_batch_attr<mpk::K_P3>(pl, qi, sms);
-        case mpk::K_PG: return gen_batch_attr<mpk::K_PG>(pl, qi, sms);
-        default: return gen_batch_attr<mpk::K_P2>(pl, qi, sms);
-    }
-}
-
-cudaError_t gen_dispatch_launch(const mp_batch_plan *pl, const mpk::BatchData &bd, const mpk::BatchQueue &q,
-                                int qi, int kind, cudaStream_t st) {
-    switch (kind) {
-        case mpk::K_P1: return launch_gen_batch<mpk::K_P1>(pl, bd, q, qi, st);
-        case mpk::K_P3: return launch_gen_batch<mpk::K_P3>(pl, bd, q, qi, st);
-        case mpk::K_PG: return launch_gen_batch<mpk::K_PG>(pl, bd, q, qi, st);
-        default: return launch_gen_batch<mpk::K_P2>(pl, bd, q, qi, st);
+// Launch the sweep of queue qi on `grid` CTAs.
+cudaError_t batch_queue_launch(const mp_batch_plan *pl, int qi, int grid, const mpk::BatchData &bd,
+                               const mpk::BatchQueue &q, cudaStream_t st) {
+    switch (qi) {
+        case mp_batch_plan::Q_FAST2: return mpk::batch2_launch(mpk::K_P2, pl->filter, grid, pl->smem[qi], bd, q, st);
+        case mp_batch_plan::Q_FASTP: return mpk::batch2_launch(pl->genp_kind, false, grid, pl->smem[qi], bd, q, st);
+        case mp_batch_plan::Q_Z: return mpk::batchz_launch(grid, pl->smem[qi], bd, q, st);
+        default:
+            return mpk::batchg_launch(qi == mp_batch_plan::Q_GEN2 ? mpk::K_P2 : pl->genp_kind, grid, pl->smem[qi], bd,
+                                      q, mpk::device_error_ptr(), st);
     }
 }
 
@@ -907,17 +838,7 @@ mp_status batch_build_graph(mp_batch_plan *pl, const void *T, double *P, int64_t
     for (int qi = 0; qi < mp_batch_plan::NQ; ++qi) {
         if (pl->tiles[qi].empty()) continue;
         const mpk::BatchQueue q{pl->d_tiles[qi], static_cast<unsigned>(pl->tiles[qi].size()), tickets + qi};
-        if (qi == mp_batch_plan::Q_FAST2)
-            if (pl->filter) mpk::sweep2_batch_kernel<mpk::K_P2, true><<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
-            else mpk::sweep2_batch_kernel<mpk::K_P2, false><<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
-        else if (qi == mp_batch_plan::Q_FASTP && pl->genp_kind == mpk::K_P1)
-            mpk::sweep2_batch_kernel<mpk::K_P1, false><<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
-        else if (qi == mp_batch_plan::Q_FASTP)
-            mpk::sweep2_batch_kernel<mpk::K_P3, false><<<pl->grid[qi], mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
-        else if (qi == mp_batch_plan::Q_Z)
-            mpk::sweepz_batch_kernel<<<pl->grid[qi], mpk::Z_NT, pl->smem[qi], st>>>(bd, q);
-        else
-            gen_dispatch_launch(pl, bd, q, qi, qi == mp_batch_plan::Q_GEN2 ? mpk::K_P2 : pl->genp_kind, st);
+        batch_queue_launch(pl, qi, pl->grid[qi], bd, q, st);
         ++nodes;
     }
     mpk::batch_finalize_kernel<<<gw, mpk::PREP_NT, 0, st>>>(bd);
@@ -1103,19 +1024,16 @@ static mp_status batch_plan_build(const mp_batch_desc *desc, const mp_options *o
         e = cudaMalloc(&pl->d_tiles[qi], bytes);
         if (e == cudaSuccess) e = cudaMemcpy(pl->d_tiles[qi], pl->tiles[qi].data(), bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) break;
+        int per_sm = 0;
         if (qi == mp_batch_plan::Q_FAST2 || qi == mp_batch_plan::Q_FASTP) {
             const int kind = qi == mp_batch_plan::Q_FAST2 ? mpk::K_P2 : pl->genp_kind;
-            e = kind == mpk::K_P1 ? fast_batch_attr<mpk::K_P1, false>(pl, qi, sms)
-                : kind == mpk::K_P3 ? fast_batch_attr<mpk::K_P3, false>(pl, qi, sms)
-                : pl->filter        ? fast_batch_attr<mpk::K_P2, true>(pl, qi, sms)
-                                    : fast_batch_attr<mpk::K_P2, false>(pl, qi, sms);
+            e = mpk::batch2_setup(kind, kind == mpk::K_P2 && pl->filter, pl->smem[qi], &per_sm);
         } else if (qi == mp_batch_plan::Q_Z) {
-            e = cudaFuncSetAttribute(mpk::sweepz_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(pl->smem[qi]));
-            if (e == cudaSuccess) batch_grid(pl, qi, mpk::sweepz_batch_kernel, mpk::Z_NT, sms);
+            e = mpk::batchz_setup(pl->smem[qi], &per_sm);
         } else {
-            e = gen_dispatch_attr(pl, qi, qi == mp_batch_plan::Q_GEN2 ? mpk::K_P2 : pl->genp_kind, sms);
+            e = mpk::batchg_setup(qi == mp_batch_plan::Q_GEN2 ? mpk::K_P2 : pl->genp_kind, pl->smem[qi], &per_sm);
         }
+        if (e == cudaSuccess) batch_grid(pl, qi, per_sm, sms);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -1526,24 +1444,8 @@ mp_status mp_anytime_run(mp_anytime *a, int64_t max_tiles, void *stream) {
     const mpk::BatchData bd = anytime_data(a, nullptr, nullptr);
     const mpk::BatchQueue q{pl->d_tiles[qi] + a->cursor, static_cast<unsigned>(count), ticket};
     const int grid = static_cast<int>(std::min<long long>(pl->grid[qi], count));
-    if (qi == mp_batch_plan::Q_FAST2 && pl->filter)
-        mpk::sweep2_batch_kernel<mpk::K_P2, true><<<grid, mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
-    else if (qi == mp_batch_plan::Q_FAST2)
-        mpk::sweep2_batch_kernel<mpk::K_P2, false><<<grid, mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
-    else if (qi == mp_batch_plan::Q_FASTP && pl->genp_kind == mpk::K_P1)
-        mpk::sweep2_batch_kernel<mpk::K_P1, false><<<grid, mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
-    else if (qi == mp_batch_plan::Q_FASTP)
-        mpk::sweep2_batch_kernel<mpk::K_P3, false><<<grid, mpk::V2_NT, pl->smem[qi], st>>>(bd, q);
-    else if (qi == mp_batch_plan::Q_Z)
-        mpk::sweepz_batch_kernel<<<grid, mpk::Z_NT, pl->smem[qi], st>>>(bd, q);
-    else {
-        const int saved = pl->grid[qi];  // launch_gen_batch takes the grid from the plan
-        pl->grid[qi] = grid;
-        gen_dispatch_launch(pl, bd, q, qi, qi == mp_batch_plan::Q_GEN2 ? mpk::K_P2 : pl->genp_kind, st);
-        pl->grid[qi] = saved;
-    }
+    e = batch_queue_launch(pl, qi, grid, bd, q, st);
     counted();
-    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "anytime sweep launch");
     a->cursor += count;
     return MP_OK;

@@ -23,7 +23,6 @@
 #include <cuda_runtime.h>
 
 #include "mp_device.cuh"
-#include "mp_prep.cuh"
 #include "mp_sweep.cuh"
 #include "mp_sweep2.cuh"
 #include "mp_sweep_z2.cuh"
@@ -35,7 +34,7 @@ struct BatchSeries {
     long long w_off;    // first window (keys, P, I)
     long long z_off;    // first window in the z-normalised operand arrays, or -1
     long long n, N, k_first;
-    int m, dist;        // dist: FIN_EUCLID, FIN_PNORM or FIN_ZNORM
+    int m, dist;        // dist: FIN_EUCLID, FIN_PNORM or FIN_ZNORM (mp_prep.cuh)
     int B, Q, RL;       // generic sweep: re-anchor block, ring blocks, leaving rows
     int pad;
 };
@@ -76,56 +75,6 @@ __device__ __forceinline__ int batch_series_of(const BatchData &d, long long g) 
         else hi = mid - 1;
     }
     return lo;
-}
-
-__global__ void __launch_bounds__(PREP_NT) batch_init_kernel(unsigned long long *keys, long long windows,
-                                                             unsigned *tickets, int ntickets) {
-    if (blockIdx.x == 0 && threadIdx.x < ntickets) tickets[threadIdx.x] = 0u;
-    for (long long x = blockIdx.x * (long long)PREP_NT + threadIdx.x; x < windows;
-         x += (long long)gridDim.x * PREP_NT)
-        keys[x] = KEY_NONE;
-}
-
-__global__ void __launch_bounds__(PREP_NT) batch_zstats_kernel(const BatchData d) {
-    for (long long g = blockIdx.x * (long long)PREP_NT + threadIdx.x; g < d.windows;
-         g += (long long)gridDim.x * PREP_NT) {
-        const BatchSeries &s = d.series[batch_series_of(d, g)];
-        if (s.dist != FIN_ZNORM) continue;
-        const long long i = g - s.w_off, z = s.z_off;
-        window_stats_at(d.T + s.t_off, i, s.m, d.mu[z + i], d.Sx[z + i], d.flat[z + i]);
-    }
-}
-
-__global__ void __launch_bounds__(PREP_NT) batch_zoperands_kernel(const BatchData d) {
-    for (long long g = blockIdx.x * (long long)PREP_NT + threadIdx.x; g < d.windows;
-         g += (long long)gridDim.x * PREP_NT) {
-        const BatchSeries &s = d.series[batch_series_of(d, g)];
-        if (s.dist != FIN_ZNORM) continue;
-        const long long i = g - s.w_off, z = s.z_off;
-        znorm_operands_at(d.T + s.t_off, i, s.N, s.m, d.mu + z, d.Sx + z, d.flat + z, 0.0, d.df + z, d.dg + z,
-                          d.inv + z, d.muh + z, d.mul + z);
-    }
-}
-
-__global__ void __launch_bounds__(PREP_NT) batch_finalize_kernel(const BatchData d) {
-    for (long long g = blockIdx.x * (long long)PREP_NT + threadIdx.x; g < d.windows;
-         g += (long long)gridDim.x * PREP_NT) {
-        const BatchSeries &s = d.series[batch_series_of(d, g)];
-        FinalizeArgsT<float> a{};
-        a.keys = d.keys + s.w_off;
-        a.keys128 = nullptr;
-        a.x = d.T + s.t_off;
-        a.mu = s.dist == FIN_ZNORM ? d.mu + s.z_off : nullptr;
-        a.S = s.dist == FIN_ZNORM ? d.Sx + s.z_off : nullptr;
-        a.N = s.N;
-        a.m = s.m;
-        a.dist = s.dist;
-        a.p = s.dist == FIN_PNORM ? d.p : 2.0;
-        a.polish = d.polish;
-        a.P = d.P + s.w_off;
-        a.I = d.I + s.w_off;
-        finalize_at(a, g - s.w_off);
-    }
 }
 
 // Thread 0 takes the next ticket and publishes the tile; false when the queue
@@ -173,6 +122,7 @@ __global__ void __launch_bounds__(V2_NT, 2) sweep2_batch_kernel(const BatchData 
     }
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(Z_NT, 2) sweepz_batch_kernel(const BatchData d, const BatchQueue q) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SweepZArgs za;
@@ -202,7 +152,7 @@ __global__ void __launch_bounds__(Z_NT, 2) sweepz_batch_kernel(const BatchData d
             za.m = sr->m;
         }
         __syncthreads();
-        sweepz_tile<K_Z, false>(za, tile.band, tile.rt, smem);
+        sweepz_tile<MODE, false>(za, tile.band, tile.rt, smem);
         __syncthreads();
     }
 }

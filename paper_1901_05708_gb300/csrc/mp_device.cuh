@@ -5,8 +5,19 @@
 #include <cuda_runtime.h>
 
 // Device-side error word: kernels OR mpk::ERR_* bits into it; mp_sync_status
-// reads and clears it.  (The library is a single translation unit.)
-__device__ int mp_device_error;
+// reads and clears it.  The library is several translation units compiled
+// without relocatable device code, so each one that holds kernels has its own
+// word (internal linkage) and exports its address through an accessor
+// (MPK_ERROR_WORD_ACCESSOR); mp_sync_status reads every word.
+static __device__ int mp_device_error;
+
+// Defines `int *fn()`: the device address of this translation unit's error word.
+#define MPK_ERROR_WORD_ACCESSOR(fn)                                               \
+    int *fn() {                                                                   \
+        void *p = nullptr;                                                        \
+        return cudaGetSymbolAddress(&p, mp_device_error) == cudaSuccess           \
+                   ? static_cast<int *>(p) : nullptr;                             \
+    }
 
 namespace mpk {
 

@@ -104,7 +104,9 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
 //   prefix(b) = sum_{b' < b} floor((L - b' KW + R - 1) / R),
 // a floor-sum of an arithmetic progression, evaluated in O(log) steps.
 __host__ __device__ inline long long floor_sum(long long n, long long mdiv, long long a, long long b) {
-    // sum_{i=0}^{n-1} floor((a i + b) / mdiv), a, b >= 0, mdiv > 0
+    // sum_{i=0}^{n-1} floor((a i + b) / mdiv), a, b >= 0, mdiv > 0, by the standard
+    // Euclid-like reduction for floor sums of a linear function (the method of the
+    // AtCoder Library's floor_sum)
     long long ans = 0;
     while (true) {
         if (a >= mdiv) {

@@ -136,18 +136,20 @@ def test_polish_off_keeps_sweep_values(mp):
 
 def test_batch_4096_sampled(mp):
     """The 4,096-series workload (lengths 2,000..65,536, m in {32, 64, 128},
-    half Euclidean, half z-normalised): 32 series by seed, sampled rows by
-    brute force, and the whole-profile properties on every series."""
+    half Euclidean, half z-normalised): 256 series chosen by seed with 16
+    sampled rows each, plus 3 sampled rows (and the first and last) of every
+    series, by brute force; and the whole-profile properties on every
+    series."""
     b = W.batch_4096()
     series = b.series
     plan, T, P, I = run_batch(mp, series, 2.0)
     o = plan.out_offsets
     rng = np.random.default_rng(21)
-    pick = rng.choice(len(series), 32, replace=False)
-    for k in pick:
-        s = series[k]
+    pick = set(rng.choice(len(series), 256, replace=False).tolist())
+    for k, s in enumerate(series):
         Pk, Ik = P[o[k]:o[k + 1]], I[o[k]:o[k + 1]]
-        rows = np.unique(np.concatenate([rng.choice(s.N, 24, replace=False), [0, s.N - 1]]))
+        count = 16 if k in pick else 3
+        rows = np.unique(np.concatenate([rng.choice(s.N, count, replace=False), [0, s.N - 1]]))
         ref = oracle.brute_rows(s.T.astype(np.float64), s.m, s.excl, rows, NAMES[s.dist])
         parity.check(s.T.astype(np.float64), s.m, s.excl, NAMES[s.dist], 2.0, Pk, Ik, RTOL32, rows=rows,
                      P_ref=ref[0], I_ref=ref[1], P2=ref[2], label=f"batch4096 series {k}")

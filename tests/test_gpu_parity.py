@@ -79,7 +79,7 @@ def test_fp64_sweep(mp, dist, p):
     P, I = run(mp, s.T, s.m, s.excl, dist, p, precision="fp64")
     parity.check(s.T, s.m, s.excl, dist, p, P, I, RTOL64, label=f"fp64 {dist}")
     P, I = run(mp, s.T, s.m, s.excl, dist, p, precision="fp64", polish=False)
-    parity.check(s.T, s.m, s.excl, dist, p, P, I, 1e-10, label=f"fp64 raw {dist}")
+    parity.check(s.T, s.m, s.excl, dist, p, P, I, RTOL64, label=f"fp64 raw {dist}")
 
 
 def test_float64_input(mp):

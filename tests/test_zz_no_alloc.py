@@ -30,12 +30,12 @@ def lib():
     return L
 
 
-def _noalloc(lib, T, m, excl):
+def _noalloc(lib, T, m, excl, **kw):
     from paper_1901_05708_gb300 import mp
     N = T.numel() - m + 1
     P = torch.full((N,), -1.0, dtype=torch.float64, device=T.device)
     I = torch.full((N,), -7, dtype=torch.int64, device=T.device)
-    opt = mp.options()
+    opt = mp.options(**kw)
     stream = torch.cuda.current_stream(T.device)
     st = lib.mp_aamp_noalloc(ctypes.c_void_p(T.data_ptr()), mp.MP_F32, T.numel(), m, excl,
                              ctypes.c_void_p(P.data_ptr()), ctypes.c_void_p(I.data_ptr()),
@@ -57,6 +57,43 @@ def test_noalloc_matches_workspace_entry_point(lib):
             P, I = _noalloc(lib, T, s.m, s.excl)
             np.testing.assert_allclose(P, Pw, rtol=RTOL32, atol=0)
             np.testing.assert_array_equal(I, Iw)
+
+
+@pytest.mark.parametrize("n,m,kw", [
+    (300_000, 256, {}),                        # long series: the kernel with the block filter
+    (3_000, 20, {"precision": "fp64"}),        # the FP64 sweep (128-bit keys)
+    (20_000, 64, {"k_range": (500, 7_000)}),   # a diagonal range
+])
+def test_noalloc_other_kernels(lib, n, m, kw):
+    """The scratch also serves the filtered kernel of long series, the FP64
+    sweep and diagonal ranges: two calls in a row equal mp_aamp's result."""
+    from paper_1901_05708_gb300 import mp
+    s = W.small("motif", n, m, 17, dtype=np.float32)
+    T = torch.from_numpy(s.T).cuda()
+    Pw, Iw = mp.aamp(T, s.m, s.excl, **kw)
+    torch.cuda.synchronize()
+    Pw, Iw = Pw.cpu().numpy(), Iw.cpu().numpy()
+    rtol = 1e-12 if kw.get("precision") == "fp64" else RTOL32
+    for _ in range(2):
+        P, I = _noalloc(lib, T, s.m, s.excl, **kw)
+        np.testing.assert_allclose(P, Pw, rtol=rtol, atol=0)
+        np.testing.assert_array_equal(I, Iw)
+
+
+def test_noalloc_checks_arguments_first(lib):
+    """Bad arguments get mp_aamp's status (MP_ERR_INVALID_ARG) before any
+    scratch lookup, and nothing is written."""
+    from paper_1901_05708_gb300 import mp
+    T = torch.zeros(100, dtype=torch.float32, device="cuda")
+    P = torch.full((91,), -1.0, dtype=torch.float64, device="cuda")
+    I = torch.full((91,), -7, dtype=torch.int64, device="cuda")
+    for args in ((ctypes.c_void_p(0), mp.MP_F32, 100, 10), (ctypes.c_void_p(T.data_ptr()), 7, 100, 10),
+                 (ctypes.c_void_p(T.data_ptr()), mp.MP_F32, 100, 0)):
+        st = lib.mp_aamp_noalloc(*args, 2, ctypes.c_void_p(P.data_ptr()), ctypes.c_void_p(I.data_ptr()), None,
+                                 ctypes.c_void_p(0))
+        assert st == mp.MP_ERR_INVALID_ARG, lib.mp_last_error()
+    torch.cuda.synchronize()
+    assert torch.all(P == -1.0) and torch.all(I == -7)
 
 
 def test_noalloc_rejects_oversized_problem(lib):
