@@ -10,7 +10,9 @@ device-resident T: conversion, diagonal sweep, FP64 polish, P and I.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Prints one JSON line (rank 0).  Under torchrun each rank computes its own
-series (seed + rank): weak scaling, no collective on the data path.
+series (seed + rank): weak scaling, no collective on the data path; with
+--shard the ranks split one series' diagonals (Algorithm 1's k loop) and
+merge the partial profiles with two MIN all-reduces: strong scaling.
 --impl reference times the FP64 CPU oracle (Algorithm 1, OpenMP over the
 host cores) on a bounded diagonal range of the same series.
 """
@@ -167,16 +169,16 @@ def oracle_sample(series: W.Series, target_s: float = 12.0):
             return oracle.pnorm(T, series.m, series.excl, series.p, k_range=k_range)
         return oracle.acamp_centred(T, series.m, series.excl, k_range=k_range)
 
-    # calibrate on a short range
-    kc = min(256, max(1, series.N - k0))
-    t0 = time.perf_counter()
-    sweep((k0, k0 + kc))
-    dt = time.perf_counter() - t0
-    rate = kc * series.N / max(dt, 1e-6)  # cells/s, roughly
-    K = int(min(series.N - k0, max(kc, target_s * rate / series.N)))
-    t0 = time.perf_counter()
-    sweep((k0, k0 + K))
-    dt = time.perf_counter() - t0
+    # calibrate on a short range, then grow the range until the run takes at
+    # least half the target (thread start-up makes short calibrations pessimistic)
+    K = min(256, max(1, series.N - k0))
+    while True:
+        t0 = time.perf_counter()
+        sweep((k0, k0 + K))
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * target_s or K >= series.N - k0:
+            break
+        K = int(min(series.N - k0, max(2 * K, K * target_s / max(dt, 1e-3))))
     cells = sum(series.N - k for k in range(k0, k0 + K))
     return {"value": cells / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{series.name}: diagonals {k0}..{k0 + K - 1} ({cells:.3e} cells) in {dt:.2f} s",
@@ -387,6 +389,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--k-range", type=int, nargs=2, default=None,
                     help="sweep only diagonals [k0, k1) (for timing the FP64 sweep on a slice)")
+    ap.add_argument("--shard", action="store_true",
+                    help="split one series' diagonals over the ranks and merge (strong scaling); "
+                         "default: every rank its own series (weak scaling)")
     ap.add_argument("--fp64-diagonals", type=int, default=8192,
                     help="also time the FP64 sweep on this many diagonals (0: skip)")
     args = ap.parse_args()
@@ -415,7 +420,13 @@ def main():
             dist.destroy_process_group()
         return
     make, desc, instr_per_cell = WORKLOADS[args.workload]
-    series = make(1 + rank, args.n)
+    shard_range = None
+    if args.shard:  # one series, its diagonals split over the ranks (strong scaling)
+        from paper_1901_05708_gb300 import shard as SH
+        series = make(1, args.n)
+        shard_range = SH.diagonal_ranges(series.excl + 1, series.N, ws)[rank]
+    else:           # every rank its own series (weak scaling)
+        series = make(1 + rank, args.n)
     dname = {W.EUCLID: "euclid", W.PNORM: "pnorm", W.ZNORM: "znorm"}[series.dist]
     T_host = torch.from_numpy(series.T).pin_memory()
     T = T_host.to(dev)
@@ -428,9 +439,15 @@ def main():
     kw = {"precision": args.precision}
     if args.k_range:
         kw["k_range"] = tuple(args.k_range)
+    if shard_range is not None:
+        kw["k_range"] = shard_range
 
-    def step():
-        mp.profile(T, series.m, series.excl, dname, series.p, out=(P, I), **kw)
+    def step(Tin=None):
+        mp.profile(T if Tin is None else Tin, series.m, series.excl, dname, series.p, out=(P, I), **kw)
+        if shard_range is not None and ws > 1:  # the one exchange: two MIN all-reduces of the partial profiles
+            Pm, Im = SH.allreduce_merge(P, I)
+            P.copy_(Pm)
+            I.copy_(Im)
 
     for _ in range(args.warmup):
         step()
@@ -475,7 +492,11 @@ def main():
     if args.k_range:
         lo, hi = max(args.k_range[0], series.excl + 1), min(args.k_range[1], series.N)
         cells = sum(series.N - k for k in range(lo, hi))
-    value = ws * cells * args.steps / (total_ms * 1e-3) / 1e9
+    job_cells = cells if shard_range is not None else ws * cells  # cells of the whole job per step
+    if shard_range is not None:  # this rank's own diagonals (for its sweep kernel's roofline)
+        lo, hi = shard_range
+        cells = (hi - lo) * (2 * series.N - lo - hi + 1) // 2
+    value = job_cells * args.steps / (total_ms * 1e-3) / 1e9
 
     # ---- end to end through the public API with host buffers -------------------
     P_host = torch.empty(N, dtype=torch.float64).pin_memory()
@@ -487,17 +508,17 @@ def main():
     e0.record(stream)
     for _ in range(e2e_steps):
         T_dev2.copy_(T_host, non_blocking=True)
-        mp.profile(T_dev2, series.m, series.excl, dname, series.p, out=(P, I), **kw)
+        step(T_dev2)
         P_host.copy_(P, non_blocking=True)
         I_host.copy_(I, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    e2e_value = ws * cells / (e2e_ms * 1e-3) / 1e9
+    e2e_value = job_cells / (e2e_ms * 1e-3) / 1e9
 
     # ---- the FP64 sweep on a slice of the same diagonals (kernel events only) ----------
     fp64 = None
-    if args.precision == "fp32" and not args.k_range and args.fp64_diagonals > 0:
+    if args.precision == "fp32" and not args.k_range and shard_range is None and args.fp64_diagonals > 0:
         k0 = series.excl + 1
         k1 = min(series.N, k0 + args.fp64_diagonals)
         kw64 = {"precision": "fp64", "k_range": (k0, k1)}
@@ -549,7 +570,8 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "scaling": "strong" if shard_range is not None else "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic", "config": workload_config(series, desc, args.precision), "roofline": roof,
             "clocks": clk,
             "gpu_launches": int(launches),
@@ -557,6 +579,9 @@ def main():
                     "d2h_bytes_per_step": int(N * 16), "ms_per_step": e2e_ms}}
     if args.k_range:
         line["config"]["k_range"] = list(args.k_range)
+    if shard_range is not None:
+        line["config"]["parallelism"] = f"diagonal ranges over {ws} ranks, merged by two MIN all-reduces"
+        line["config"]["rank0_diagonals"] = list(shard_range)
     if fp64 is not None:
         fp64["fp32_over_fp64"] = achieved / fp64["value"]
         line["fp64_sweep"] = fp64

@@ -81,7 +81,7 @@ typedef enum { MP_DIST_EUCLID = 0, MP_DIST_PNORM = 1, MP_DIST_ZNORM = 2 } mp_dis
  * not apply.  The filter only skips candidates that cannot pass, so with or
  * without it the results are the same bit for bit.
  * The others force a choice (MP_ERR_UNSUPPORTED where it does not apply);
- * mp_autotune times them (not MP_VARIANT_ZRAW).
+ * mp_autotune times them (not MP_VARIANT_ZRAW or MP_VARIANT_ZF).
  * MP_VARIANT_ZRAW runs Algorithm 2 as printed (Lemma 3): the dot product
  * C = sum t_{i+l} t_{j+l} carried along each diagonal and
  * rho = (C - A_i A_j / m) / sqrt(S_i S_j) with the window sums A, in the
@@ -89,7 +89,12 @@ typedef enum { MP_DIST_EUCLID = 0, MP_DIST_PNORM = 1, MP_DIST_ZNORM = 2 } mp_dis
  * (every `reanchor` rows, default 512 in FP32, 256 in FP64).  The numerator
  * cancels when a window's mean is large against its spread, which the
  * centred covariance of the other kernels avoids: it exists to measure that
- * loss and the speed of the paper's form, not for use. */
+ * loss and the speed of the paper's form, not for use.
+ * MP_VARIANT_ZF is Sec. 4.3's comparison on the same raw sums: candidates are
+ * ordered by F = (A_i A_j - m C) |A_i A_j - m C| / (S_i S_j) (= -m^2 rho |rho|,
+ * increasing with DZ; no square root per cell) and the winner's value is
+ * DZ^2 = 2m + 2 sign(F) sqrt(|F|); FP32 or FP64 sweep, re-anchored like
+ * MP_VARIANT_ZRAW; also an ablation. */
 typedef enum {
     MP_VARIANT_AUTO = 0,
     MP_VARIANT_FAST_FILTER = 1,  /* two-stream kernel with the block filter (p = 2); */
@@ -99,8 +104,10 @@ typedef enum {
                                  /* shared memory limits m to about 12,000)          */
     MP_VARIANT_TALL = 4,         /* tall-tile kernel: float-float sums, tiles of      */
                                  /* max(8192, 8m) rows (p in {1, 2, 3}; long windows) */
-    MP_VARIANT_ZRAW = 5          /* ablation, z-normalised only, FP32 or FP64 sweep:  */
+    MP_VARIANT_ZRAW = 5,         /* ablation, z-normalised only, FP32 or FP64 sweep:  */
                                  /* Algorithm 2's raw sums (see below)               */
+    MP_VARIANT_ZF = 6            /* ablation, z-normalised only, FP32 or FP64 sweep:  */
+                                 /* raw sums compared through F (Sec. 4.3)           */
 } mp_variant;
 
 typedef struct mp_options {

@@ -146,7 +146,7 @@ mp_status check_problem(Problem &pb, const void *T, const double *P, const int64
         return fail(MP_ERR_INVALID_ARG, "precision %d", pb.opt.precision);
     if (pb.opt.reanchor < 0) return fail(MP_ERR_INVALID_ARG, "reanchor %d < 0", pb.opt.reanchor);
     if (pb.opt.polish != 0 && pb.opt.polish != 1) return fail(MP_ERR_INVALID_ARG, "polish %d", pb.opt.polish);
-    if (pb.opt.variant < MP_VARIANT_AUTO || pb.opt.variant > MP_VARIANT_ZRAW)
+    if (pb.opt.variant < MP_VARIANT_AUTO || pb.opt.variant > MP_VARIANT_ZF)
         return fail(MP_ERR_INVALID_ARG, "variant %d", pb.opt.variant);
     if (pb.opt.k_begin < 0) return fail(MP_ERR_INVALID_ARG, "k_begin %lld < 0", (long long)pb.opt.k_begin);
     if (!T || !P || !I) return fail(MP_ERR_INVALID_ARG, "NULL T, P or I");
@@ -365,6 +365,8 @@ mp_status check_call(Problem &pb, const void *T, const double *P, const int64_t 
         return fail(MP_ERR_UNSUPPORTED, "the generic kernel is the FP32 Euclidean / p-norm sweep");
     if (v == MP_VARIANT_ZRAW && pb.dist != MP_DIST_ZNORM)
         return fail(MP_ERR_UNSUPPORTED, "the raw-sum variant is Algorithm 2's, for the z-normalised distance");
+    if (v == MP_VARIANT_ZF && pb.dist != MP_DIST_ZNORM)
+        return fail(MP_ERR_UNSUPPORTED, "the F comparison is Sec. 4.3's, for the z-normalised distance");
     if (v == MP_VARIANT_TALL && !tall_applies(pb))
         return fail(MP_ERR_UNSUPPORTED, "the tall-tile kernel is the FP32 sweep for p in {1, 2, 3}");
     return MP_OK;
@@ -426,7 +428,19 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
             SweepEvents ev(st);
             if (g.tiles > 0) counted();
             const bool zraw = pb.opt.variant == MP_VARIANT_ZRAW;
-            if (pb.dist == MP_DIST_ZNORM && f64 && zraw) {
+            const bool zf = pb.opt.variant == MP_VARIANT_ZF;
+            if (pb.dist == MP_DIST_ZNORM && f64 && zf) {
+                mpk::VarF64ZF v{x64, reinterpret_cast<const double *>(w + L.mu),
+                                reinterpret_cast<const double *>(w + L.S),
+                                reinterpret_cast<const unsigned char *>(w + L.flat), pb.m,
+                                reinterpret_cast<mpk::Key128 *>(w + L.keys128), err};
+                e = mpk::launch_simple(g, v, pb.opt.reanchor > 0 ? pb.opt.reanchor : 256, st);
+            } else if (pb.dist == MP_DIST_ZNORM && zf) {
+                mpk::VarF32ZF v{reinterpret_cast<const float *>(w + L.hi), reinterpret_cast<const float *>(w + L.muf),
+                                reinterpret_cast<const float *>(w + L.inv), pb.m,
+                                reinterpret_cast<unsigned long long *>(w + L.keys)};
+                e = mpk::launch_simple(g, v, pb.opt.reanchor > 0 ? pb.opt.reanchor : 512, st);
+            } else if (pb.dist == MP_DIST_ZNORM && f64 && zraw) {
                 mpk::VarF64ZRaw v{x64, reinterpret_cast<const double *>(w + L.mu),
                                   reinterpret_cast<const double *>(w + L.S),
                                   reinterpret_cast<const unsigned char *>(w + L.flat), pb.m,
@@ -496,6 +510,7 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
     fa.dist = pb.dist == MP_DIST_EUCLID ? mpk::FIN_EUCLID : pb.dist == MP_DIST_PNORM ? mpk::FIN_PNORM : mpk::FIN_ZNORM;
     fa.p = pb.dist == MP_DIST_PNORM ? pb.p : 2.0;
     fa.polish = pb.opt.polish;
+    fa.fkey = pb.dist == MP_DIST_ZNORM && pb.opt.variant == MP_VARIANT_ZF;
     fa.P = P;
     fa.I = reinterpret_cast<long long *>(I);
     mpk::finalize_kernel<<<grid_for(pb.N, mpk::PREP_NT), mpk::PREP_NT, 0, st>>>(fa);

@@ -211,10 +211,25 @@ struct FinalizeArgsT {
     int dist;
     double p;
     int polish;
+    int fkey;                        // z-norm keys hold the order image of F (Sec. 4.3), not 1 - rho
     double *P;
     long long *I;
 };
 using FinalizeArgs = FinalizeArgsT<double>;
+
+// Inverse of the order-preserving images f_order_bits (mp_simple.cuh).
+__device__ __forceinline__ float f_from_order_bits(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+__device__ __forceinline__ double f_from_order_bits(unsigned long long u) {
+    return __longlong_as_double(static_cast<long long>((u >> 63) ? (u & ~(1ull << 63)) : ~u));
+}
+
+// DZ^2 from F = -m^2 rho |rho|: 2m + 2 sign(F) sqrt(|F|) (Sec. 4.3, Appendix A).
+__device__ __forceinline__ double dz2_from_f(double F, int m) {
+    const double r = sqrt(fabs(F));
+    return 2.0 * m + 2.0 * (F < 0 ? -r : r);
+}
 
 // |v|^p; the products are rounded one by one (no contraction into the caller's
 // sum), so every kernel that polishes gets the same bits.
@@ -296,15 +311,18 @@ __device__ __forceinline__ void finalize_at(const FinalizeArgsT<X> &a, long long
         const unsigned long long key = a.keys[x];
         none = key == KEY_NONE;
         lo = key & 0xffffffffull;
-        const float v = __uint_as_float(static_cast<unsigned>(key >> 32));
-        // z-norm keys hold 1 - rho; DZ^2 = 2m(1 - rho) (Lemma 3)
-        sweep_score = a.dist == FIN_ZNORM ? 2.0 * a.m * static_cast<double>(v) : static_cast<double>(v);
+        const unsigned vb = static_cast<unsigned>(key >> 32);
+        const float v = __uint_as_float(vb);
+        // z-norm keys hold 1 - rho; DZ^2 = 2m(1 - rho) (Lemma 3); or F
+        if (a.fkey) sweep_score = dz2_from_f(static_cast<double>(f_from_order_bits(vb)), a.m);
+        else sweep_score = a.dist == FIN_ZNORM ? 2.0 * a.m * static_cast<double>(v) : static_cast<double>(v);
     } else {
         const Key128 key = a.keys128[x];
         none = key.hi == KEY_NONE;
         lo = key.lo;
         const double v = __longlong_as_double(static_cast<long long>(key.hi));
-        sweep_score = a.dist == FIN_ZNORM ? 2.0 * a.m * v : v;
+        if (a.fkey) sweep_score = dz2_from_f(f_from_order_bits(key.hi), a.m);
+        else sweep_score = a.dist == FIN_ZNORM ? 2.0 * a.m * v : v;
     }
     if (none) {
         a.P[x] = __longlong_as_double(0x7ff0000000000000ll);  // +inf

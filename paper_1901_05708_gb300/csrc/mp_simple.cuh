@@ -316,3 +316,91 @@ struct VarF32ZRaw {
 };
 
 }  // namespace mpk
+
+namespace mpk {
+
+// ---- z-normalised, raw sums compared through F (Sec. 4.3, Appendix A; an ablation) ---
+// The paper's cheaper comparison: instead of DZ^2, each candidate is ordered by
+//   F_{i,j} = (A_i B_j - m C_{i,j}) |A_i B_j - m C_{i,j}| / (S_i S_j)
+// with Lemma 3's window sums A = m mu, the dot product C carried along the
+// diagonal as in VarF64ZRaw / VarF32ZRaw, and S the centred sums of squares
+// (the denominator read as (B_j - B_j^2 / m), the square Lemma 3 has).  F is
+// -m^2 rho |rho|, increasing in DZ, and needs no square root per cell; the
+// winner's distance is DZ^2 = 2m + 2 sign(F) sqrt(|F|) (that formula's left
+// side read as DZ^2).  F is signed, so keys hold an order-preserving map of its
+// bits (f_order_bits) and the finalize inverts it (FinalizeArgs::fkey).
+
+// Unsigned image of a float / double that orders like the value (negative
+// values: all bits flipped; others: the sign bit set).
+__device__ __forceinline__ unsigned f_order_bits(float f) {
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ unsigned long long f_order_bits(double f) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(f));
+    return (b >> 63) ? ~b : (b | (1ull << 63));
+}
+
+struct VarF64ZF {
+    using Real = double;
+    struct State { double c; };
+    const double *x, *mu, *S;
+    const unsigned char *flat;
+    int m;
+    Key128 *keys;
+    int *err;
+    __device__ static double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+    __device__ State anchor(long long i, long long k) const {
+        double acc = 0.0;
+        for (int l = 0; l < m; ++l) acc = fma(x[i + l], x[i + k + l], acc);
+        return State{acc};
+    }
+    __device__ void step(State &s, long long i, long long k) const {
+        const long long a = i - 1, b = i + k - 1;
+        s.c = fma(x[a + m], x[b + m], fma(-x[a], x[b], s.c));
+    }
+    __device__ double score(const State &s, long long i, long long k) const {
+        if (flat[i] || flat[i + k]) return __longlong_as_double(0x7ff8000000000000ll);  // NaN
+        const double A = m * mu[i], B = m * mu[i + k];
+        const double num = fma(A, B, -static_cast<double>(m) * s.c);  // A_i B_j - m C
+        return num * fabs(num) / (S[i] * S[i + k]);
+    }
+    __device__ void emit(long long target, double val, long long k, int right) const {
+        const unsigned long long hi = f_order_bits(val);
+        if (keys[target].hi != KEY_NONE && hi > keys[target].hi) return;
+        if (!atomic_min_key128(&keys[target], hi, static_cast<unsigned long long>(2 * k + right)))
+            atomicOr(err, ERR_CAS_SPIN);
+    }
+};
+
+struct VarF32ZF {
+    using Real = float;
+    struct State { float c; };
+    const float *t;    // FP32 series
+    const float *muf;  // FP32 window means
+    const float *inv;  // 1 / sqrt(S); NaN for a flat window
+    int m;
+    unsigned long long *keys;
+    __device__ static float inf() { return __int_as_float(0x7f800000); }
+    __device__ State anchor(long long i, long long k) const {
+        float acc = 0.f;
+        for (int l = 0; l < m; ++l) acc = fmaf(t[i + l], t[i + k + l], acc);
+        return State{acc};
+    }
+    __device__ void step(State &s, long long i, long long k) const {
+        const long long a = i - 1, b = i + k - 1;
+        s.c = fmaf(t[a + m], t[b + m], fmaf(-t[a], t[b], s.c));
+    }
+    __device__ float score(const State &s, long long i, long long k) const {
+        const float fm = static_cast<float>(m);
+        const float num = fmaf(fm * muf[i], fm * muf[i + k], -fm * s.c);  // A_i B_j - m C
+        const float w = inv[i] * inv[i + k];                                // NaN if flat
+        return num * fabsf(num) * (w * w);
+    }
+    __device__ void emit(long long target, float val, long long k, int right) const {
+        if (!(val < __int_as_float(0x7f800000))) return;
+        atomicMin(&keys[target], make_key(f_order_bits(val), k, right));
+    }
+};
+
+}  // namespace mpk

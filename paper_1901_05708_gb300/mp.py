@@ -29,8 +29,8 @@ MP_OK, MP_ERR_INVALID_ARG, MP_ERR_UNSUPPORTED, MP_ERR_WORKSPACE, MP_ERR_CUDA, MP
 MP_F32, MP_F64 = 0, 1
 MP_PREC_FP32, MP_PREC_FP64 = 0, 1
 MP_DIST_EUCLID, MP_DIST_PNORM, MP_DIST_ZNORM = 0, 1, 2
-MP_VARIANT_AUTO, MP_VARIANT_FAST_FILTER, MP_VARIANT_FAST, MP_VARIANT_GENERIC, MP_VARIANT_TALL, MP_VARIANT_ZRAW = \
-    0, 1, 2, 3, 4, 5
+(MP_VARIANT_AUTO, MP_VARIANT_FAST_FILTER, MP_VARIANT_FAST, MP_VARIANT_GENERIC, MP_VARIANT_TALL, MP_VARIANT_ZRAW,
+ MP_VARIANT_ZF) = range(7)
 
 EXPORTS = ("mp_options_default", "mp_workspace_size", "mp_aamp", "mp_pnorm", "mp_acamp",
            "mp_sync_status", "mp_last_error", "mp_status_string", "mp_version", "mp_launch_count",
@@ -163,7 +163,8 @@ def options(precision: str = "fp32", reanchor: int = 0, polish: bool = True,
     """mp_options for the calls below.  variant (include/mp.h, mp_variant): MP_VARIANT_AUTO;
     MP_VARIANT_FAST_FILTER / MP_VARIANT_FAST: the two-stream kernel with / without its block
     filter (the z-normalised kernel with / without its filter for acamp); MP_VARIANT_GENERIC;
-    MP_VARIANT_TALL; MP_VARIANT_ZRAW: Algorithm 2's raw-sum form, an ablation (acamp only)."""
+    MP_VARIANT_TALL; MP_VARIANT_ZRAW: Algorithm 2's raw-sum form, an ablation (acamp only);
+    MP_VARIANT_ZF: the same raw sums compared through Sec. 4.3's F, an ablation (acamp only)."""
     o = Options()
     load().mp_options_default(ctypes.byref(o))
     o.precision = {"fp32": MP_PREC_FP32, "fp64": MP_PREC_FP64}[precision]

@@ -11,12 +11,19 @@ Acceptance (for FP32 sweeps rtol = 1e-5, for FP64 sweeps rtol = 1e-12):
         valid neighbour within tolerance.
 
 These are the contract's rules, for the polished profile (the default) and
-for raw sweep values alike.  One property of the FP32 z-normalised kernel is
-stated separately and applies only to its raw sweep value (``raw_z32=True``):
-it resolves q = 1 - rho = DZ^2 / 2m to an absolute Q_ATOL_Z32 (the FP32
-rounding of the window scale factors and of their product), so the raw value
-DZ = sqrt(2m q) of a near-identical pair of windows may be off by up to
-sqrt(P^2 + 2m Q_ATOL_Z32) - P; that term widens rule (i) of a raw check only.
+for raw sweep values alike.  One property of the FP32 sweeps is stated
+separately and applies only to their raw sweep values (``raw_fp32=True``):
+they carry the score (P^p for the pure / p-norm distances, q = 1 - rho =
+DZ^2 / 2m for the z-normalised one), whose FP32 rounding is absolute in that
+space, so near P = 0 (flat runs, identical windows) the raw value's error is
+set by the score's resolution, not by P:
+  - pure / p-norm: the score is resolved to S_ATOL = rtol m sd(diff T)^p (the
+    floor of rule (i), taken in score space), so the raw P may be off by up to
+    (P^p + S_ATOL)^(1/p) - P;
+  - z-normalised: q is resolved to an absolute Q_ATOL_Z32 (the FP32 rounding
+    of the window scale factors and of their product), so the raw DZ may be
+    off by up to sqrt(P^2 + 2m Q_ATOL_Z32) - P.
+These terms widen rule (i) (and (ii)) of a raw FP32 check only.
 """
 from __future__ import annotations
 
@@ -36,7 +43,7 @@ def atol_for(T, m, dist, p, rtol):
 
 
 def check(T, m, excl, dist, p, P, I, rtol, rows=None, P_ref=None, I_ref=None, P2=None,
-          label="", raw_z32=False):
+          label="", raw_fp32=False):
     """Compare (P, I) (numpy, full length N) with the oracle on `rows`
     (all rows if None).  Reference values may be passed in; otherwise brute
     force rows are computed here.  Returns a dict of error statistics."""
@@ -53,9 +60,15 @@ def check(T, m, excl, dist, p, P, I, rtol, rows=None, P_ref=None, I_ref=None, P2
     Pfin = np.where(np.isfinite(P_ref), P_ref, 0.0)
     tol = rtol * Pfin + atol
     tol_p = tol
-    if raw_z32 and dist == "znorm":
-        # the raw FP32 z-normalised value (rule (i) only; see the module docstring)
+    if raw_fp32 and dist == "znorm":
+        # the raw FP32 z-normalised value (rules (i), (ii) only; see the module docstring)
         tol_p = tol + np.sqrt(Pfin ** 2 + 2 * m * Q_ATOL_Z32) - Pfin
+    elif raw_fp32:
+        # the raw FP32 pure / p-norm value: the score's absolute resolution
+        pp = 2.0 if dist == "euclid" else p
+        sd = np.std(np.diff(T)) if T.size > 1 else 0.0
+        s_atol = rtol * m * max(sd, 1e-300) ** pp
+        tol_p = tol + (Pfin ** pp + s_atol) ** (1.0 / pp) - Pfin
 
     none = I_ref < 0
     assert np.all(Ig[none] == -1), f"{label}: rows without candidates got an index"

@@ -82,10 +82,12 @@ def test_argument_checks_need_no_gpu(lib):
     o.precision = 9
     assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG
     lib.mp_options_default(ctypes.byref(o))
-    o.variant = mp.MP_VARIANT_ZRAW + 1
+    o.variant = mp.MP_VARIANT_ZF + 1
     assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG             # no such variant
     o.variant = mp.MP_VARIANT_ZRAW
     assert _call_aamp(lib, opt=o) == E.MP_ERR_UNSUPPORTED             # the raw-sum form is Algorithm 2's
+    o.variant = mp.MP_VARIANT_ZF
+    assert _call_aamp(lib, opt=o) == E.MP_ERR_UNSUPPORTED             # the F comparison is Sec. 4.3's
     o.variant = mp.MP_VARIANT_GENERIC                                   # the z-normalised distance has no generic kernel
     vp = ctypes.c_void_p
     assert lib.mp_acamp(vp(0x1000), 0, 100, 10, 2, vp(0x2000), vp(0x3000), vp(0x10000), 1 << 30,

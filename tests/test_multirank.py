@@ -88,3 +88,65 @@ def test_two_ranks_gloo(tmp_path, dist_name, p):
         P, I = oracle.acamp_centred(T, m, excl)
     np.testing.assert_array_equal(got["P"], P)
     np.testing.assert_array_equal(got["I"], I)
+
+
+def _rank_main_libmp(rank, world, port, T, m, excl, out_path, dist_name, p):
+    """One rank: the CUDA library sweeps this rank's diagonal range on the
+    GPU; the parts are merged over gloo on host tensors."""
+    import torch
+    import torch.distributed as dist
+    from paper_1901_05708_gb300 import mp
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        N = T.size - m + 1
+        lo, hi = shard.diagonal_ranges(excl + 1, N, world)[rank]
+        Tt = torch.from_numpy(T).cuda()
+        P, I = mp.profile(Tt, m, excl, dist_name, p, k_range=(lo, hi))
+        torch.cuda.synchronize()
+        mp.sync_status()
+        Pm, Im = shard.allreduce_merge(P.cpu(), I.cpu())
+        if rank == 0:
+            np.savez(out_path, P=Pm.numpy(), I=Im.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dist_name,p,kind", [("euclid", 2.0, "int"), ("pnorm", 1.0, "int"),
+                                               ("euclid", 2.0, "walk"), ("znorm", 2.0, "walk")])
+def test_two_ranks_libmp(tmp_path, dist_name, p, kind):
+    """Two processes run the CUDA library on their diagonal ranges (here on
+    the one GPU, one after the other or side by side: the sweeps never wait on
+    each other) and merge with two MIN all-reduces over gloo.  Integer series:
+    the merged profile equals the single call bit for bit; random walks: it
+    passes the parity rules against the oracle."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import torch.multiprocessing as tmp
+    import parity
+    from paper_1901_05708_gb300 import mp
+    n, m, excl = 20_000, 64, 16
+    T = W.small(kind, n, m, 23, dtype=np.float32).T
+    out = str(tmp_path / "merged.npz")
+    port = _free_port()
+    ctx = tmp.get_context("spawn")
+    procs = [ctx.Process(target=_rank_main_libmp, args=(r, 2, port, T, m, excl, out, dist_name, p))
+             for r in range(2)]
+    for pr in procs:
+        pr.start()
+    for pr in procs:
+        pr.join(timeout=300)
+        assert pr.exitcode == 0
+    got = np.load(out)
+    Tt = torch.from_numpy(T).cuda()
+    P1, I1 = mp.profile(Tt, m, excl, dist_name, p)
+    torch.cuda.synchronize()
+    P1, I1 = P1.cpu().numpy(), I1.cpu().numpy()
+    if kind == "int":
+        np.testing.assert_array_equal(got["P"], P1)
+        np.testing.assert_array_equal(got["I"], I1)
+    else:
+        parity.check(T, m, excl, dist_name, p, got["P"], got["I"], 1e-5, label=f"two ranks {dist_name}")

@@ -71,7 +71,7 @@ def test_tie_inside_winner_zone_passes():
 def test_znorm_strict_unless_raw_fp32():
     """The z-normalised rules are the contract's (1e-5 relative, rtol sqrt(m)
     floor): a P off by more than that fails, unless the check is explicitly of
-    the FP32 kernel's raw sweep value (raw_z32), whose stated q resolution
+    the FP32 kernel's raw sweep value (raw_fp32), whose stated q resolution
     widens rule (i) only."""
     s = W.small("walk", 900, 16, 8)
     T = s.T.copy()
@@ -85,4 +85,24 @@ def test_znorm_strict_unless_raw_fp32():
     Pg[x] = P[x] + tol + 0.5 * loose
     with pytest.raises(AssertionError):
         parity.check(T, s.m, s.excl, "znorm", 2.0, Pg, I, 1e-5, label="polished")
-    parity.check(T, s.m, s.excl, "znorm", 2.0, Pg, I, 1e-5, label="raw", raw_z32=True)
+    parity.check(T, s.m, s.excl, "znorm", 2.0, Pg, I, 1e-5, label="raw", raw_fp32=True)
+
+
+def test_pnorm_raw_score_resolution():
+    """Near P = 0 (a flat run: exact zero distances) a raw FP32 p-norm value
+    carries the score's absolute rounding, amplified by the p-th root: a
+    residue of 1e-9 in the score is P = 1e-3 for p = 3.  That fails the
+    contract's rules and passes only as an explicit raw FP32 check."""
+    s = W.small("flat", 2000, 32, 51)
+    T = s.T
+    P, I = oracle.brute(T, s.m, s.excl, "pnorm", 3.0)
+    x = int(np.argmin(P))
+    assert P[x] == 0.0
+    Pg = P.copy()
+    Pg[x] = 1e-9 ** (1 / 3)
+    with pytest.raises(AssertionError):
+        parity.check(T, s.m, s.excl, "pnorm", 3.0, Pg, I, 1e-5, label="polished")
+    parity.check(T, s.m, s.excl, "pnorm", 3.0, Pg, I, 1e-5, label="raw", raw_fp32=True)
+    Pg[x] = 0.1  # far beyond the score's resolution: fails either way
+    with pytest.raises(AssertionError):
+        parity.check(T, s.m, s.excl, "pnorm", 3.0, Pg, I, 1e-5, label="raw", raw_fp32=True)
