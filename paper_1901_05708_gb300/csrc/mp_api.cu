@@ -282,7 +282,7 @@ mp_status run_tall(const Problem &pb, const Layout &L, char *ws, cudaStream_t st
     a.m = pb.m;
     a.L = pb.N - pb.k_first;
     a.nb = (pb.k_end - pb.k_first + mpk::Z_KW - 1) / mpk::Z_KW;
-    a.S = mpk::z_rows_per_tile(pb.m);
+    a.S = mpk::z_rows_per_tile(pb.m, false);
     a.tiles = mpk::z_prefix(a.L, a.nb, a.S);
     if (a.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", a.tiles);
     if (a.tiles <= 0) return MP_OK;
@@ -474,7 +474,7 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
                 za.m = pb.m;
                 za.L = pb.N - pb.k_first;
                 za.nb = (pb.k_end - pb.k_first + mpk::Z_KW - 1) / mpk::Z_KW;
-                za.S = mpk::z_rows_per_tile(pb.m);
+                za.S = mpk::z_rows_per_tile(pb.m, true);
                 za.tiles = mpk::z_prefix(za.L, za.nb, za.S);
                 if (za.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", za.tiles);
                 const bool filter = pb.opt.variant == MP_VARIANT_FAST_FILTER ||
@@ -710,6 +710,10 @@ struct mp_batch_plan {
            o_mul = 0, ws_bytes = 0;
     // graph cache
     cudaStream_t cap = nullptr;
+    // one capture stream per queue, forked from `cap` and joined before the
+    // finalize, so that the queues' persistent kernels overlap in the graph
+    cudaStream_t qst[NQ] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[NQ] = {};
     cudaGraphExec_t exec = nullptr;
     const void *g_T = nullptr;
     const void *g_P = nullptr;
@@ -724,6 +728,11 @@ void batch_free(mp_batch_plan *pl) {
     if (!pl) return;
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->cap) cudaStreamDestroy(pl->cap);
+    for (int q = 0; q < mp_batch_plan::NQ; ++q) {
+        if (pl->qst[q]) cudaStreamDestroy(pl->qst[q]);
+        if (pl->ev_join[q]) cudaEventDestroy(pl->ev_join[q]);
+    }
+    if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
     if (pl->d_series) cudaFree(pl->d_series);
     if (pl->d_wstart) cudaFree(pl->d_wstart);
     for (auto *t : pl->d_tiles)
@@ -850,10 +859,17 @@ mp_status batch_build_graph(mp_batch_plan *pl, const void *T, double *P, int64_t
         mpk::batch_zoperands_kernel<<<gw, mpk::PREP_NT, 0, st>>>(bd);
         nodes += 2;
     }
+    // the queues' sweeps on forked streams: each starts after the statistics, the
+    // finalize after all of them (CTAs of the next queue fill the SMs that the
+    // tail of another leaves idle)
+    cudaEventRecord(pl->ev_fork, st);
     for (int qi = 0; qi < mp_batch_plan::NQ; ++qi) {
         if (pl->tiles[qi].empty()) continue;
         const mpk::BatchQueue q{pl->d_tiles[qi], static_cast<unsigned>(pl->tiles[qi].size()), tickets + qi};
-        batch_queue_launch(pl, qi, pl->grid[qi], bd, q, st);
+        cudaStreamWaitEvent(pl->qst[qi], pl->ev_fork, 0);
+        batch_queue_launch(pl, qi, pl->grid[qi], bd, q, pl->qst[qi]);
+        cudaEventRecord(pl->ev_join[qi], pl->qst[qi]);
+        cudaStreamWaitEvent(st, pl->ev_join[qi], 0);
         ++nodes;
     }
     mpk::batch_finalize_kernel<<<gw, mpk::PREP_NT, 0, st>>>(bd);
@@ -951,7 +967,7 @@ static mp_status batch_plan_build(const mp_batch_desc *desc, const mp_options *o
             b.z_off = pl->zwindows;
             pl->zwindows += b.N;
             qi = mp_batch_plan::Q_Z;
-            batch_tiles(q[qi], si, L, mpk::Z_KW, static_cast<int>(mpk::z_rows_per_tile(b.m)));
+            batch_tiles(q[qi], si, L, mpk::Z_KW, static_cast<int>(mpk::z_rows_per_tile(b.m, true)));
         } else if (b.m % 32 == 0 && mpk::sweep2_smem_bytes(b.m, mpk::V2_QMAX) <= mpk::V2_SMEM_MAX &&
                    (p2 || pl->genp_kind == mpk::K_P1 || pl->genp_kind == mpk::K_P3)) {
             qi = p2 ? mp_batch_plan::Q_FAST2 : mp_batch_plan::Q_FASTP;
@@ -1051,6 +1067,12 @@ static mp_status batch_plan_build(const mp_batch_desc *desc, const mp_options *o
         if (e == cudaSuccess) batch_grid(pl, qi, per_sm, sms);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming);
+    for (int qi = 0; qi < mp_batch_plan::NQ && e == cudaSuccess; ++qi) {
+        if (pl->tiles[qi].empty()) continue;
+        e = cudaStreamCreateWithFlags(&pl->qst[qi], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_join[qi], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         batch_free(pl);
         return cuda_fail(e, "creating the batch plan");

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(Z_NT, 2) sweepz_batch_kernel(const BatchData d
             za.L = sr->N - sr->k_first;
             za.nb = (za.L + Z_KW - 1) / Z_KW;
             za.tiles = 0;
-            za.S = z_rows_per_tile(sr->m);
+            za.S = z_rows_per_tile(sr->m, MODE == K_Z);
             za.m = sr->m;
         }
         __syncthreads();

@@ -44,14 +44,23 @@ namespace mpk {
 constexpr int Z_NT = 128;             // threads per CTA
 constexpr int Z_D = 8;                // diagonals per thread
 constexpr int Z_KW = Z_NT * Z_D;      // diagonals per band
-constexpr int Z_S = 8192;             // rows per tile (at least; S = max(Z_S, 8m) rounded to 2 RC)
+constexpr int Z_S = 8192;             // rows per tile of the long-window p-norm modes (at least; max(Z_S, 8m))
+constexpr int Z_SZ = 65536;           // rows per tile of the z-normalised sweep (at least)
 constexpr int Z_RC = 512;             // rows per stream per chunk
 
-// rows per tile for window length m
-__host__ __device__ inline long long z_rows_per_tile(long long m) {
+// Rows per tile for window length m: max(base, 8m) rounded up to 2 RC, with
+// base Z_SZ for the z-normalised sweep (zn) and Z_S for the p-norm modes.  A
+// tile pays one O(m) float-float anchor per stream and carries the state over
+// S / 2 rows: the z-normalised float-float covariance drifts little (measured
+// raw error 1.2e-6 at S = 8192, 2.9e-6 at S = 65536 on the C4 series) and
+// taller tiles cut the anchors' share of the sweep from about a fifth to a
+// few percent; the p-norm modes' sums of m terms of both signs drift more, so
+// their tiles stay shorter.
+__host__ __device__ inline long long z_rows_per_tile(long long m, bool zn) {
     long long S = 8 * m;
     S = (S + 2 * Z_RC - 1) / (2 * Z_RC) * (2 * Z_RC);
-    return S < Z_S ? Z_S : S;
+    const long long base = zn ? Z_SZ : Z_S;
+    return S < base ? base : S;
 }
 
 struct SweepZArgs {
@@ -61,7 +70,7 @@ struct SweepZArgs {
     const float *df, *dg, *inv;       // operands (inv = NaN for a flat window)
     unsigned long long *keys;
     long long n, N, k_first, k_end, L, nb, tiles;
-    long long S;                      // rows per tile (z_rows_per_tile(m))
+    long long S;                      // rows per tile (z_rows_per_tile(m, mode == K_Z))
     int m;
     float p;                          // exponent of the p-norm modes (unused for K_P1 / K_P2 / K_P3's own term)
 };

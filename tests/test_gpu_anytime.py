@@ -27,8 +27,12 @@ def mp():
 
 
 def fp32_tol(s, dist, p, P):
-    """The FP32 sweep's resolution at P (parity rule i): rtol 1e-5, the absolute
-    floor and, for z-normalised rows, the FP32 resolution of q."""
+    """The FP32 sweep's ordering resolution at P, for comparing partial
+    profiles with each other: rtol 1e-5, the absolute floor and, for
+    z-normalised rows, the FP32 resolution of q (candidates closer than this
+    may be ordered either way, so a later partial profile may hold a neighbour
+    that much farther).  The finished profile is checked against the oracle
+    with the contract's rules."""
     rtol = 1e-5
     Pf = np.where(np.isfinite(P), P, 0.0)
     tol = rtol * Pf + parity.atol_for(s.T, s.m, dist, p, rtol)
@@ -72,6 +76,11 @@ def test_partial_profiles_tighten_to_the_full_one(mp, dist, p, m):
     np.testing.assert_array_equal(I, Iref)
     np.testing.assert_array_equal(P, Pref)
     a.close()
+    # the finished profile against the oracle's brute force (the contract's rules)
+    rows = np.unique(np.concatenate([np.random.default_rng(5).choice(s.N, 200, replace=False), [0, s.N - 1]]))
+    ref = oracle.brute_rows(T64, s.m, s.excl, rows, dist, p)
+    parity.check(T64, s.m, s.excl, dist, p, P, I, 1e-5, rows=rows, P_ref=ref[0], I_ref=ref[1], P2=ref[2],
+                 label=f"anytime {dist} p={p}")
 
 
 def test_checkpoint_and_restore(mp):
