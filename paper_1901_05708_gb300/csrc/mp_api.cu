@@ -254,14 +254,14 @@ mp_status run_sweep2(const Problem &pb, const Layout &L, char *ws, cudaStream_t 
     a.k_first = pb.k_first;
     a.k_end = pb.k_end;
     a.m = pb.m;
-    a.Q = mpk::V2_QMAX;  // B = m / 4: a multiple of 8 since m % 32 == 0
+    a.Q = mpk::v2_ring_blocks(kind_of(pb.dist, pb.p));  // B = m / Q: a multiple of 8 since m % 32 == 0
     a.B = pb.m / a.Q;
     a.L = pb.N - pb.k_first;
     a.nb = (pb.k_end - pb.k_first + mpk::V2_KW - 1) / mpk::V2_KW;
     a.tiles = mpk::v2_prefix(a.L, a.nb);
     if (a.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", a.tiles);
     if (a.tiles <= 0) return MP_OK;
-    const size_t smem = mpk::sweep2_smem_bytes(a.m, a.Q);
+    const size_t smem = mpk::sweep2_smem_bytes(a.m, mpk::V2_QMAX);
     const int kind = kind_of(pb.dist, pb.p);
     SweepEvents ev(st);
     if (kind != mpk::K_P2) return launched(mpk::sweep2_p13_launch(kind, a, smem, st), "two-stream sweep launch");

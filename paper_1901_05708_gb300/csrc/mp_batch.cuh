@@ -113,8 +113,8 @@ __global__ void __launch_bounds__(V2_NT, 2) sweep2_batch_kernel(const BatchData 
             sa.nb = (sa.L + V2_KW - 1) / V2_KW;
             sa.tiles = 0;
             sa.m = sr->m;
-            sa.Q = V2_QMAX;
-            sa.B = sr->m / V2_QMAX;
+            sa.Q = v2_ring_blocks(KIND);
+            sa.B = sr->m / sa.Q;
         }
         __syncthreads();
         sweep2_tile<KIND, FILTER>(sa, tile.band, tile.rt, smem);

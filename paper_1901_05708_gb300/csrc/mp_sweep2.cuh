@@ -1,6 +1,6 @@
 // a3-a5, fast path: the Euclidean diagonal sweep (Algorithm 1) and the
 // p-norm sweep for p = 1 and 3 (Algorithm 3) for FP32 series with m a
-// multiple of 32 (re-anchor interval B = m / 4, Q = 4).
+// multiple of 32 (re-anchor interval B = m / Q: Q = 2 for p = 2, 4 for p = 1, 3).
 //
 // Same decomposition as the generic kernel (bands of KW diagonals, row
 // tiles, D adjacent diagonals per thread), shaped for the FP32 pipes:
@@ -16,7 +16,9 @@
 //    where, after each exact anchor A, E restarts at 0 and F' at -A; E is
 //    also the sum of the current block of B entering terms that feeds the
 //    ring of exact block sums (see the generic kernel), so the re-anchor
-//    costs nothing per cell.
+//    costs nothing per cell.  For p = 2 the ring holds Q = 2 blocks (one
+//    re-anchor every m / 2 rows) and the other half of its space holds the
+//    filter pass's saved state.
 //
 //  * Tagged minima.  Each score is tagged with its diagonal slot d in the low
 //    log2(D) mantissa bits (one integer op per cell); tagged scores are still
@@ -33,7 +35,9 @@
 //    of the group), per diagonal (both sums only grow within a block); unless
 //    some lane's bound could beat the loosest threshold of the rows and
 //    columns its block feeds, the block is done without scores, tags or
-//    slots.  Otherwise the block is replayed from the saved state with the
+//    slots.  Otherwise the block is replayed from the state saved in shared
+//    memory at the block's start (stores on the load / store pipe instead of
+//    32 register copies on the FMA pipe, and 32 registers fewer) with the
 //    tracked bookkeeping above.
 //
 //  * Shared memory holds, per tile, the j-side series as float2 pairs
@@ -56,7 +60,10 @@ constexpr int V2_KW = V2_NT * V2_D;    // diagonals per band
 constexpr int V2_H = 1024;             // rows per stream
 constexpr int V2_R = 2 * V2_H;         // rows per tile
 constexpr int V2_LBR = 4;              // filter pass: rows per lower bound (divides V2_D)
-constexpr int V2_QMAX = 4;             // ring blocks per diagonal
+constexpr int V2_QMAX = 4;             // ring space per diagonal, in blocks
+// ring blocks in use: 2 for p = 2 (re-anchor every m / 2 rows; the other half
+// of the ring's space holds the filter pass's saved state), 4 for p = 1, 3
+__host__ __device__ constexpr int v2_ring_blocks(int kind) { return kind == K_P2 ? 2 : V2_QMAX; }
 // shared memory of one CTA such that two fit on an SM (228 KB, 1 KB reserved per CTA)
 constexpr size_t V2_SMEM_MAX = 113 * 1024;
 
@@ -158,7 +165,7 @@ inline size_t sweep2_smem_bytes(int m, int Q) {
     const size_t ni = V2_H + m + 16 + 2;  // + the one-element shift of IT, kept even
     const size_t nc = v2_cpos(V2_KW + 2 * V2_H + 16);
     return (nj + ni) * sizeof(float2) + (2 * V2_H + 4 + nc) * sizeof(float) +
-           static_cast<size_t>(Q) * V2_D * V2_NT * sizeof(float2);
+           static_cast<size_t>(Q) * V2_D * V2_NT * sizeof(float2) + 16;
 }
 
 
@@ -464,9 +471,16 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
         // walks and on i.i.d. data alike.
         bool track = true;
         if (kFilter) {
-            float2 E0[V2_D], F0[V2_D];
+            // the block's starting state, kept in shared memory for a replay
+            // (the ring starts 8 bytes past a 16-byte boundary: round up; smem has 16 bytes of slack)
+            float4 *sv = reinterpret_cast<float4 *>(
+                             (reinterpret_cast<uintptr_t>(ring + 2 * V2_D * V2_NT) + 15) & ~static_cast<uintptr_t>(15)) +
+                         tid;
 #pragma unroll
-            for (int d = 0; d < V2_D; ++d) { E0[d] = E[d]; F0[d] = F[d]; }
+            for (int p2 = 0; p2 < V2_D / 2; ++p2) {
+                sv[p2 * V2_NT] = make_float4(E[2 * p2].x, E[2 * p2].y, E[2 * p2 + 1].x, E[2 * p2 + 1].y);
+                sv[(p2 + V2_D / 2) * V2_NT] = make_float4(F[2 * p2].x, F[2 * p2].y, F[2 * p2 + 1].x, F[2 * p2 + 1].y);
+            }
             const int slot0 = anchor_slot, next0 = next_anchor;
             // Within the block E and F' only grow (every step adds a term >= 0,
             // and rounding is monotone), so for a group of rows g+1 .. g+G,
@@ -487,7 +501,7 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
                 const float4 *ite4 = reinterpret_cast<const float4 *>(IT + ub + m + 1);
                 float2 Eg[V2_D];  // E at the row before the current group
 #pragma unroll
-                for (int d = 0; d < V2_D; ++d) Eg[d] = E0[d];
+                for (int d = 0; d < V2_D; ++d) Eg[d] = E[d];
 #pragma unroll
                 for (int ul = 1; ul <= V2_D; ++ul) {
                     const float4 l4 = itl4[(ul - 1) >> 1], e4 = ite4[(ul - 1) >> 1];
@@ -562,7 +576,13 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args &a, long long band,
                                                    __int_as_float(__float_as_int(bmb) & tag_mask) <= tmb);
             if (__builtin_expect(track, 0)) {  // replay the block from the saved state, tracked
 #pragma unroll
-                for (int d = 0; d < V2_D; ++d) { E[d] = E0[d]; F[d] = F0[d]; }
+                for (int p2 = 0; p2 < V2_D / 2; ++p2) {
+                    const float4 e4 = sv[p2 * V2_NT], f4 = sv[(p2 + V2_D / 2) * V2_NT];
+                    E[2 * p2] = make_float2(e4.x, e4.y);
+                    E[2 * p2 + 1] = make_float2(e4.z, e4.w);
+                    F[2 * p2] = make_float2(f4.x, f4.y);
+                    F[2 * p2 + 1] = make_float2(f4.z, f4.w);
+                }
                 anchor_slot = slot0;
                 next_anchor = next0;
             }
