@@ -106,8 +106,12 @@ typedef enum {
                                  /* max(8192, 8m) rows (p in {1, 2, 3}; long windows) */
     MP_VARIANT_ZRAW = 5,         /* ablation, z-normalised only, FP32 or FP64 sweep:  */
                                  /* Algorithm 2's raw sums (see below)               */
-    MP_VARIANT_ZF = 6            /* ablation, z-normalised only, FP32 or FP64 sweep:  */
+    MP_VARIANT_ZF = 6,           /* ablation, z-normalised only, FP32 or FP64 sweep:  */
                                  /* raw sums compared through F (Sec. 4.3)           */
+    MP_VARIANT_CACHED = 7        /* the autotuner's cached choice for this problem    */
+                                 /* class (kernel, reanchor, tile_rows) if present,  */
+                                 /* else AUTO; in a batch plan, each z-normalised    */
+                                 /* series' cached tile_rows                         */
 } mp_variant;
 
 typedef struct mp_options {
@@ -117,6 +121,13 @@ typedef struct mp_options {
     int32_t polish;       /* 1 (default): P[i] recomputed in FP64 as d(i, I[i])   */
                           /* 0: P is the sweep's own (FP32 or FP64) value          */
     int32_t variant;      /* FP32 sweep kernel, mp_variant (default MP_VARIANT_AUTO) */
+    int32_t tile_rows;    /* rows per tile of the tall-tile kernels (the FP32      */
+                          /* z-normalised kernel and MP_VARIANT_TALL): 0 (default) */
+                          /* = max(65536, 8m) for z-normalised, max(8192, 8m) for  */
+                          /* tall; else a multiple of 1024.  Taller tiles pay the  */
+                          /* O(m) anchor less often and carry the FP32 state over  */
+                          /* more rows; shorter ones give short series more tiles. */
+                          /* Must be 0 for the other kernels (MP_ERR_UNSUPPORTED). */
     int64_t k_begin;      /* sweep only diagonals k >= k_begin (default 0)        */
     int64_t k_end;        /* ... and k < k_end (<= 0 means no upper bound).       */
                           /* Disjoint ranges computed separately and merged with  */
@@ -376,7 +387,8 @@ mp_status mp_anytime_destroy(mp_anytime *a);
  * default re-anchor interval and at intervals of 16, 32 and 64 rows that
  * divide m into at most 8 blocks, each distinct interval once; the tall-tile
  * kernel for m >= 512; for the z-normalised distance its kernel with and
- * without the filter)
+ * without the filter, each at the default tile height and at 16,384 and 4,096
+ * rows per tile where those are shorter than the default and than N)
  * on the caller's series, each candidate once to warm up and once timed (the
  * sweep kernel alone, CUDA events on `stream`; the call synchronises it).
  * slice_cells = 0 times the whole sweep; slice_cells > 0 only the first
@@ -387,7 +399,8 @@ mp_status mp_anytime_destroy(mp_anytime *a);
  * max_times entries, -1 for one that does not apply), and *n_times their
  * number.  Results are cached in memory per (device name, dist, dtype, m,
  * log2 N, p); a cached problem returns at once without timing (*n_times = 0)
- * unless `force`.  P and I (N entries, device) are scratch for the timed runs;
+ * unless `force`.  MP_VARIANT_CACHED in later calls (and batch plans) applies
+ * a cached entry.  P and I (N entries, device) are scratch for the timed runs;
  * their content afterwards is unspecified.  Arguments and errors as mp_aamp /
  * mp_pnorm / mp_acamp (ws sized by mp_workspace_size for opt). */
 mp_status mp_autotune(int dist, const void *T, int dtype, int64_t n, int32_t m, int64_t excl, double p,

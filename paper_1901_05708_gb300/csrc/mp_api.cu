@@ -146,8 +146,10 @@ mp_status check_problem(Problem &pb, const void *T, const double *P, const int64
         return fail(MP_ERR_INVALID_ARG, "precision %d", pb.opt.precision);
     if (pb.opt.reanchor < 0) return fail(MP_ERR_INVALID_ARG, "reanchor %d < 0", pb.opt.reanchor);
     if (pb.opt.polish != 0 && pb.opt.polish != 1) return fail(MP_ERR_INVALID_ARG, "polish %d", pb.opt.polish);
-    if (pb.opt.variant < MP_VARIANT_AUTO || pb.opt.variant > MP_VARIANT_ZF)
+    if (pb.opt.variant < MP_VARIANT_AUTO || pb.opt.variant > MP_VARIANT_CACHED)
         return fail(MP_ERR_INVALID_ARG, "variant %d", pb.opt.variant);
+    if (pb.opt.tile_rows < 0 || pb.opt.tile_rows % 1024 != 0 || pb.opt.tile_rows > (1 << 30))
+        return fail(MP_ERR_INVALID_ARG, "tile_rows %d: 0 or a positive multiple of 1024", pb.opt.tile_rows);
     if (pb.opt.k_begin < 0) return fail(MP_ERR_INVALID_ARG, "k_begin %lld < 0", (long long)pb.opt.k_begin);
     if (!T || !P || !I) return fail(MP_ERR_INVALID_ARG, "NULL T, P or I");
     if (!aligned(T, pb.dtype == MP_F64 ? 8 : 4) || !aligned(P, 8) || !aligned(I, 8))
@@ -282,7 +284,7 @@ mp_status run_tall(const Problem &pb, const Layout &L, char *ws, cudaStream_t st
     a.m = pb.m;
     a.L = pb.N - pb.k_first;
     a.nb = (pb.k_end - pb.k_first + mpk::Z_KW - 1) / mpk::Z_KW;
-    a.S = mpk::z_rows_per_tile(pb.m, false);
+    a.S = pb.opt.tile_rows > 0 ? pb.opt.tile_rows : mpk::z_rows_per_tile(pb.m, false);
     a.tiles = mpk::z_prefix(a.L, a.nb, a.S);
     if (a.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", a.tiles);
     if (a.tiles <= 0) return MP_OK;
@@ -347,11 +349,26 @@ mp_status run_sweep_f32(const Problem &pb, const Layout &L, char *ws, cudaStream
     return launched(mpk::generic_launch(kind_of(pb.dist, pb.p), split, a, smem, st), "generic sweep launch");
 }
 
+// The autotuner's cached choice for this problem class, written into opt's
+// variant, reanchor and tile_rows; false if there is none (autotuning section).
+bool tune_lookup(const Problem &pb, mp_options &opt);
+
 // Every check of a one-series call that does not involve the workspace:
-// check_problem, then whether the chosen kernel variant applies.
+// check_problem, then whether the chosen kernel variant applies.  A
+// MP_VARIANT_CACHED request is resolved here (to the cached choice, else AUTO).
 mp_status check_call(Problem &pb, const void *T, const double *P, const int64_t *I, const mp_options *opt) {
     mp_status s = check_problem(pb, T, P, I, opt);
     if (s != MP_OK) return s;
+    if (pb.opt.variant == MP_VARIANT_CACHED) {
+        mp_options c = pb.opt;
+        if (tune_lookup(pb, c)) {
+            pb.opt.variant = c.variant;
+            pb.opt.reanchor = c.reanchor;
+            pb.opt.tile_rows = c.tile_rows;
+        } else {
+            pb.opt.variant = MP_VARIANT_AUTO;
+        }
+    }
     const int v = pb.opt.variant;
     // the z-normalised distance has one FP32 kernel; FAST / FAST_FILTER choose it
     // without / with its block filter
@@ -369,6 +386,13 @@ mp_status check_call(Problem &pb, const void *T, const double *P, const int64_t 
         return fail(MP_ERR_UNSUPPORTED, "the F comparison is Sec. 4.3's, for the z-normalised distance");
     if (v == MP_VARIANT_TALL && !tall_applies(pb))
         return fail(MP_ERR_UNSUPPORTED, "the tall-tile kernel is the FP32 sweep for p in {1, 2, 3}");
+    if (pb.opt.tile_rows != 0) {
+        const bool zfast = z32 && v != MP_VARIANT_ZRAW && v != MP_VARIANT_ZF && !getenv_generic();
+        const bool tall = !z32 && pb.dist != MP_DIST_ZNORM && pb.opt.precision == MP_PREC_FP32 && !fast_path_ok(pb) &&
+                          use_tall(pb);
+        if (!zfast && !tall)
+            return fail(MP_ERR_UNSUPPORTED, "tile_rows applies to the tall-tile kernels only");
+    }
     return MP_OK;
 }
 
@@ -474,7 +498,7 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
                 za.m = pb.m;
                 za.L = pb.N - pb.k_first;
                 za.nb = (pb.k_end - pb.k_first + mpk::Z_KW - 1) / mpk::Z_KW;
-                za.S = mpk::z_rows_per_tile(pb.m, true);
+                za.S = pb.opt.tile_rows > 0 ? pb.opt.tile_rows : mpk::z_rows_per_tile(pb.m, true);
                 za.tiles = mpk::z_prefix(za.L, za.nb, za.S);
                 if (za.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", za.tiles);
                 const bool filter = pb.opt.variant == MP_VARIANT_FAST_FILTER ||
@@ -779,8 +803,11 @@ mp_status batch_validate(const mp_batch_desc *d, const mp_options *opt, mp_optio
     if (o.reanchor != 0) return fail(MP_ERR_UNSUPPORTED, "batches use the default re-anchor interval");
     if (o.k_begin != 0 || o.k_end != 0) return fail(MP_ERR_UNSUPPORTED, "batches sweep whole diagonal ranges");
     if (o.polish != 0 && o.polish != 1) return fail(MP_ERR_INVALID_ARG, "polish %d", o.polish);
-    if (o.variant != MP_VARIANT_AUTO && o.variant != MP_VARIANT_FAST && o.variant != MP_VARIANT_FAST_FILTER)
-        return fail(MP_ERR_UNSUPPORTED, "batches take variant AUTO, FAST or FAST_FILTER");
+    if (o.variant != MP_VARIANT_AUTO && o.variant != MP_VARIANT_FAST && o.variant != MP_VARIANT_FAST_FILTER &&
+        o.variant != MP_VARIANT_CACHED)
+        return fail(MP_ERR_UNSUPPORTED, "batches take variant AUTO, FAST, FAST_FILTER or CACHED");
+    if (o.tile_rows < 0 || o.tile_rows % 1024 != 0 || o.tile_rows > (1 << 30))
+        return fail(MP_ERR_INVALID_ARG, "tile_rows %d: 0 or a positive multiple of 1024", o.tile_rows);
     if (d->t_offsets[0] < 0) return fail(MP_ERR_INVALID_ARG, "t_offsets[0] < 0");
     bool any_p = false;
     for (int s = 0; s < d->num_series; ++s) {
@@ -936,7 +963,7 @@ static mp_status batch_plan_build(const mp_batch_desc *desc, const mp_options *o
     pl->S = desc->num_series;
     pl->p = desc->p;
     pl->polish = o.polish;
-    pl->filter = o.variant == MP_VARIANT_FAST_FILTER;
+    pl->filter = o.variant == MP_VARIANT_FAST_FILTER;  // (CACHED: off, as AUTO, for the Euclidean queue)
     if (desc->p == 1.0) pl->genp_kind = mpk::K_P1;
     else if (desc->p == 2.0) pl->genp_kind = mpk::K_P2;
     else if (desc->p == 3.0) pl->genp_kind = mpk::K_P3;
@@ -967,7 +994,21 @@ static mp_status batch_plan_build(const mp_batch_desc *desc, const mp_options *o
             b.z_off = pl->zwindows;
             pl->zwindows += b.N;
             qi = mp_batch_plan::Q_Z;
-            batch_tiles(q[qi], si, L, mpk::Z_KW, static_cast<int>(mpk::z_rows_per_tile(b.m, true)));
+            // rows per tile: the caller's tile_rows, a cached autotuning choice for
+            // this series' problem class (MP_VARIANT_CACHED), else the default
+            long long zS = o.tile_rows > 0 ? o.tile_rows : mpk::z_rows_per_tile(b.m, true);
+            if (o.variant == MP_VARIANT_CACHED) {
+                Problem sp{};
+                sp.dist = MP_DIST_ZNORM;
+                sp.dtype = MP_F32;
+                sp.m = b.m;
+                sp.N = b.N;
+                sp.p = 2.0;
+                mp_options c = o;
+                if (tune_lookup(sp, c) && c.tile_rows > 0) zS = c.tile_rows;
+            }
+            b.zS = static_cast<int>(zS);
+            batch_tiles(q[qi], si, L, mpk::Z_KW, b.zS);
         } else if (b.m % 32 == 0 && mpk::sweep2_smem_bytes(b.m, mpk::V2_QMAX) <= mpk::V2_SMEM_MAX &&
                    (p2 || pl->genp_kind == mpk::K_P1 || pl->genp_kind == mpk::K_P3)) {
             qi = p2 ? mp_batch_plan::Q_FAST2 : mp_batch_plan::Q_FASTP;
@@ -1556,6 +1597,7 @@ namespace {
 struct TuneEntry {
     int variant = 0, reanchor = 0;
     double ms = 0;
+    int tile_rows = 0;
 };
 std::mutex g_tune_mu;
 std::map<std::string, TuneEntry> g_tune;
@@ -1573,6 +1615,17 @@ std::string tune_key(int dist, int dtype, int m, long long N, double p) {
     snprintf(buf, sizeof buf, "%s|%d|%d|%d|%d|%.6g", name.c_str(), dist, dtype, m, lg,
              dist == MP_DIST_PNORM ? p : 2.0);
     return buf;
+}
+
+bool tune_lookup(const Problem &pb, mp_options &opt) {
+    const std::string key = tune_key(pb.dist, pb.dtype, pb.m, pb.N, pb.p);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) return false;
+    opt.variant = it->second.variant;
+    opt.reanchor = it->second.reanchor;
+    opt.tile_rows = it->second.tile_rows;
+    return true;
 }
 
 }  // namespace
@@ -1597,16 +1650,16 @@ mp_status mp_autotune(int dist, const void *T, int dtype, int64_t n, int32_t m, 
     mp_status s = check_problem(pb, T, P, I, opt);
     if (s != MP_OK) return s;
     *best = pb.opt;
-    // candidates: (variant, reanchor)
-    struct Cand { int variant, reanchor; };
-    Cand cands[10];
+    // candidates: (variant, reanchor, tile_rows)
+    struct Cand { int variant, reanchor, tile_rows; };
+    Cand cands[12];
     int nc = 0;
     if (pb.dist != MP_DIST_ZNORM && pb.opt.precision == MP_PREC_FP32) {
         Problem q = pb;
         q.opt.reanchor = 0;
         if (fast_path_applies(q)) {
-            if (kind_of(pb.dist, pb.p) == mpk::K_P2) cands[nc++] = {MP_VARIANT_FAST_FILTER, 0};
-            cands[nc++] = {MP_VARIANT_FAST, 0};
+            if (kind_of(pb.dist, pb.p) == mpk::K_P2) cands[nc++] = {MP_VARIANT_FAST_FILTER, 0, 0};
+            cands[nc++] = {MP_VARIANT_FAST, 0, 0};
         }
         // the generic kernel with its default interval and with 16, 32, 64 rows,
         // each effective interval (choose_block) once
@@ -1620,18 +1673,25 @@ mp_status mp_autotune(int dist, const void *T, int dtype, int64_t n, int32_t m, 
             seen[ns++] = B;
             Problem g = pb;
             g.opt.reanchor = target;
-            if (generic_smem(g) > 0) cands[nc++] = {MP_VARIANT_GENERIC, target};
+            if (generic_smem(g) > 0) cands[nc++] = {MP_VARIANT_GENERIC, target, 0};
         }
         // the tall kernel only where its accuracy holds (see use_tall)
-        if (tall_applies(pb) && (pb.m >= 512 || generic_smem(pb) == 0)) cands[nc++] = {MP_VARIANT_TALL, 0};
+        if (tall_applies(pb) && (pb.m >= 512 || generic_smem(pb) == 0)) cands[nc++] = {MP_VARIANT_TALL, 0, 0};
     } else if (pb.dist == MP_DIST_ZNORM && pb.opt.precision == MP_PREC_FP32) {
-        cands[nc++] = {MP_VARIANT_FAST_FILTER, 0};  // the z-normalised kernel with and without its filter
-        cands[nc++] = {MP_VARIANT_FAST, 0};
+        // the z-normalised kernel with and without its filter, at the default tile
+        // height and at shorter tiles (more tiles for series that do not fill the GPU)
+        const long long S0 = mpk::z_rows_per_tile(pb.m, true);
+        for (int t : {0, 16384, 4096}) {
+            if (t > 0 && (t >= S0 || t >= pb.N)) continue;
+            cands[nc++] = {MP_VARIANT_FAST_FILTER, 0, t};
+            cands[nc++] = {MP_VARIANT_FAST, 0, t};
+        }
     }
     if (nc <= 1) {  // nothing to choose
         if (nc == 1) {
             best->variant = cands[0].variant;
             best->reanchor = cands[0].reanchor;
+            best->tile_rows = cands[0].tile_rows;
         }
         return MP_OK;
     }
@@ -1642,6 +1702,7 @@ mp_status mp_autotune(int dist, const void *T, int dtype, int64_t n, int32_t m, 
         if (it != g_tune.end()) {
             best->variant = it->second.variant;
             best->reanchor = it->second.reanchor;
+            best->tile_rows = it->second.tile_rows;
             return MP_OK;
         }
     }
@@ -1667,6 +1728,7 @@ mp_status mp_autotune(int dist, const void *T, int dtype, int64_t n, int32_t m, 
         mp_options o = pb.opt;
         o.variant = cands[c].variant;
         o.reanchor = cands[c].reanchor;
+        o.tile_rows = cands[c].tile_rows;
         o.polish = 0;
         o.k_begin = pb.k_first;
         o.k_end = pb.k_first + K;
@@ -1702,8 +1764,9 @@ mp_status mp_autotune(int dist, const void *T, int dtype, int64_t n, int32_t m, 
     if (n_times) *n_times = nc;
     best->variant = cands[bi].variant;
     best->reanchor = cands[bi].reanchor;
+    best->tile_rows = cands[bi].tile_rows;
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune[key] = TuneEntry{cands[bi].variant, cands[bi].reanchor, bestms};
+    g_tune[key] = TuneEntry{cands[bi].variant, cands[bi].reanchor, bestms, cands[bi].tile_rows};
     return MP_OK;
 }
 
@@ -1713,9 +1776,10 @@ mp_status mp_autotune_cache_save(const char *path) {
     FILE *f = fopen(path, "w");
     if (!f) return fail(MP_ERR_INVALID_ARG, "cannot write %s", path);
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    fprintf(f, "# mp autotune cache: key variant reanchor ms\n");
+    fprintf(f, "# mp autotune cache: key variant reanchor ms tile_rows\n");
     for (const auto &kv : g_tune)
-        fprintf(f, "%s %d %d %.6f\n", kv.first.c_str(), kv.second.variant, kv.second.reanchor, kv.second.ms);
+        fprintf(f, "%s %d %d %.6f %d\n", kv.first.c_str(), kv.second.variant, kv.second.reanchor, kv.second.ms,
+                kv.second.tile_rows);
     fclose(f);
     return MP_OK;
 }
@@ -1733,8 +1797,9 @@ mp_status mp_autotune_cache_load(const char *path) {
         if (line[0] == '#' || line[0] == '\n') continue;
         char key[300];
         TuneEntry t;
-        if (sscanf(line, "%299s %d %d %lf", key, &t.variant, &t.reanchor, &t.ms) != 4 ||
-            t.variant < MP_VARIANT_AUTO || t.variant > MP_VARIANT_TALL || t.reanchor < 0) {
+        const int got = sscanf(line, "%299s %d %d %lf %d", key, &t.variant, &t.reanchor, &t.ms, &t.tile_rows);
+        if ((got != 4 && got != 5) || t.variant < MP_VARIANT_AUTO || t.variant > MP_VARIANT_TALL || t.reanchor < 0 ||
+            t.tile_rows < 0 || t.tile_rows % 1024 != 0) {
             fclose(f);
             return fail(MP_ERR_INVALID_ARG, "%s:%d: malformed entry", path, lineno);
         }

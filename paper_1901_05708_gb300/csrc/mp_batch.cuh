@@ -36,7 +36,7 @@ struct BatchSeries {
     long long n, N, k_first;
     int m, dist;        // dist: FIN_EUCLID, FIN_PNORM or FIN_ZNORM (mp_prep.cuh)
     int B, Q, RL;       // generic sweep: re-anchor block, ring blocks, leaving rows
-    int pad;
+    int zS;             // z-normalised sweep: rows per tile
 };
 
 struct BatchTile {
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(Z_NT, 2) sweepz_batch_kernel(const BatchData d
             za.L = sr->N - sr->k_first;
             za.nb = (za.L + Z_KW - 1) / Z_KW;
             za.tiles = 0;
-            za.S = z_rows_per_tile(sr->m, MODE == K_Z);
+            za.S = sr->zS;
             za.m = sr->m;
         }
         __syncthreads();

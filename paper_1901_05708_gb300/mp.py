@@ -30,7 +30,7 @@ MP_F32, MP_F64 = 0, 1
 MP_PREC_FP32, MP_PREC_FP64 = 0, 1
 MP_DIST_EUCLID, MP_DIST_PNORM, MP_DIST_ZNORM = 0, 1, 2
 (MP_VARIANT_AUTO, MP_VARIANT_FAST_FILTER, MP_VARIANT_FAST, MP_VARIANT_GENERIC, MP_VARIANT_TALL, MP_VARIANT_ZRAW,
- MP_VARIANT_ZF) = range(7)
+ MP_VARIANT_ZF, MP_VARIANT_CACHED) = range(8)
 
 EXPORTS = ("mp_options_default", "mp_workspace_size", "mp_aamp", "mp_pnorm", "mp_acamp",
            "mp_sync_status", "mp_last_error", "mp_status_string", "mp_version", "mp_launch_count",
@@ -56,7 +56,7 @@ _STATUS = {0: "MP_OK", 1: "MP_ERR_INVALID_ARG", 2: "MP_ERR_UNSUPPORTED", 3: "MP_
 class Options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("precision", ctypes.c_int32),
                 ("reanchor", ctypes.c_int32), ("polish", ctypes.c_int32),
-                ("variant", ctypes.c_int32), ("k_begin", ctypes.c_int64),
+                ("variant", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("k_begin", ctypes.c_int64),
                 ("k_end", ctypes.c_int64)]
 
 
@@ -159,18 +159,21 @@ def load(path: str | None = None):
 
 
 def options(precision: str = "fp32", reanchor: int = 0, polish: bool = True,
-            k_range: tuple[int, int] | None = None, variant: int = MP_VARIANT_AUTO) -> Options:
+            k_range: tuple[int, int] | None = None, variant: int = MP_VARIANT_AUTO, tile_rows: int = 0) -> Options:
     """mp_options for the calls below.  variant (include/mp.h, mp_variant): MP_VARIANT_AUTO;
     MP_VARIANT_FAST_FILTER / MP_VARIANT_FAST: the two-stream kernel with / without its block
     filter (the z-normalised kernel with / without its filter for acamp); MP_VARIANT_GENERIC;
     MP_VARIANT_TALL; MP_VARIANT_ZRAW: Algorithm 2's raw-sum form, an ablation (acamp only);
-    MP_VARIANT_ZF: the same raw sums compared through Sec. 4.3's F, an ablation (acamp only)."""
+    MP_VARIANT_ZF: the same raw sums compared through Sec. 4.3's F, an ablation (acamp only);
+    MP_VARIANT_CACHED: the autotuner's cached choice if there is one.  tile_rows: rows per tile of
+    the tall-tile kernels (0: default; else a multiple of 1024)."""
     o = Options()
     load().mp_options_default(ctypes.byref(o))
     o.precision = {"fp32": MP_PREC_FP32, "fp64": MP_PREC_FP64}[precision]
     o.reanchor = int(reanchor)
     o.polish = 1 if polish else 0
     o.variant = int(variant)
+    o.tile_rows = int(tile_rows)
     if k_range is not None:
         o.k_begin, o.k_end = int(k_range[0]), int(k_range[1])
     return o
@@ -237,24 +240,24 @@ def _call(fn_name: str, dist: int, T, m: int, excl: int, p: float | None, opt: O
 
 
 def aamp(T, m: int, excl: int, *, precision="fp32", reanchor=0, polish=True, k_range=None, variant=0,
-         out=None, stream=None):
+         tile_rows=0, out=None, stream=None):
     """Matrix profile with the pure Euclidean distance (Algorithm 1)."""
     return _call("mp_aamp", MP_DIST_EUCLID, T, m, excl, None,
-                 options(precision, reanchor, polish, k_range, variant), out, stream)
+                 options(precision, reanchor, polish, k_range, variant, tile_rows), out, stream)
 
 
 def pnorm(T, m: int, excl: int, p: float, *, precision="fp32", reanchor=0, polish=True,
-          k_range=None, variant=0, out=None, stream=None):
+          k_range=None, variant=0, tile_rows=0, out=None, stream=None):
     """Matrix profile with the p-norm distance (Algorithm 3)."""
     return _call("mp_pnorm", MP_DIST_PNORM, T, m, excl, p,
-                 options(precision, reanchor, polish, k_range, variant), out, stream)
+                 options(precision, reanchor, polish, k_range, variant, tile_rows), out, stream)
 
 
 def acamp(T, m: int, excl: int, *, precision="fp32", reanchor=0, polish=True, k_range=None, variant=0,
-          out=None, stream=None):
+          tile_rows=0, out=None, stream=None):
     """Matrix profile with the z-normalised Euclidean distance (Algorithm 2)."""
     return _call("mp_acamp", MP_DIST_ZNORM, T, m, excl, None,
-                 options(precision, reanchor, polish, k_range, variant), out, stream)
+                 options(precision, reanchor, polish, k_range, variant, tile_rows), out, stream)
 
 
 def sync_status(stream=None):
@@ -306,7 +309,8 @@ class BatchPlan:
     I within the series.  The plan keeps its workspace, so that repeated runs
     with the same output buffers replay the same graph."""
 
-    def __init__(self, lengths, m, dist, excl, p: float = 2.0, polish: bool = True, device=None, variant: int = 0):
+    def __init__(self, lengths, m, dist, excl, p: float = 2.0, polish: bool = True, device=None, variant: int = 0,
+                 tile_rows: int = 0):
         import numpy as np
         lib = load()
         self._desc, keep = batch_desc(lengths, m, dist, excl, p)
@@ -317,7 +321,7 @@ class BatchPlan:
         np.cumsum(N, out=self.out_offsets[1:])
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index)
-        opt = options(polish=polish, variant=variant)
+        opt = options(polish=polish, variant=variant, tile_rows=tile_rows)
         h = ctypes.c_void_p()
         nbytes = ctypes.c_size_t()
         with torch.cuda.device(self.device):
@@ -519,7 +523,8 @@ def autotune(T, m: int, excl: int, dist="euclid", p: float = 2.0, precision: str
                            ctypes.c_void_p(P.data_ptr()), ctypes.c_void_p(I.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
                            ws.numel(), ctypes.byref(opt), int(slice_cells), 1 if force else 0, ctypes.byref(best),
                            times, 8, ctypes.byref(nt), ctypes.c_void_p(s.cuda_stream)))
-    return ({"precision": precision, "reanchor": best.reanchor, "variant": best.variant},
+    return ({"precision": precision, "reanchor": best.reanchor, "variant": best.variant,
+             "tile_rows": best.tile_rows},
             [times[i] for i in range(nt.value)])
 
 

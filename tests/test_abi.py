@@ -82,8 +82,16 @@ def test_argument_checks_need_no_gpu(lib):
     o.precision = 9
     assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG
     lib.mp_options_default(ctypes.byref(o))
-    o.variant = mp.MP_VARIANT_ZF + 1
+    o.variant = mp.MP_VARIANT_CACHED + 1
     assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG             # no such variant
+    lib.mp_options_default(ctypes.byref(o))
+    o.tile_rows = 1000
+    assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG             # not a multiple of 1024
+    o.tile_rows = -1024
+    assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG
+    o.tile_rows = 2048
+    assert _call_aamp(lib, opt=o) == E.MP_ERR_UNSUPPORTED             # the two-stream kernel has fixed tiles
+    lib.mp_options_default(ctypes.byref(o))
     o.variant = mp.MP_VARIANT_ZRAW
     assert _call_aamp(lib, opt=o) == E.MP_ERR_UNSUPPORTED             # the raw-sum form is Algorithm 2's
     o.variant = mp.MP_VARIANT_ZF
@@ -187,8 +195,16 @@ def test_autotune_cache_files_need_no_gpu(lib, tmp_path):
     assert lib.mp_autotune_cache_load(str(tmp_path / "missing.txt").encode()) == E.MP_ERR_INVALID_ARG
     o = mp.Options()
     lib.mp_options_default(ctypes.byref(o))
-    o.variant = 7
+    o.variant = mp.MP_VARIANT_CACHED + 1
     assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG
+    # five-field entries (with tile_rows) load too; a tile_rows that is not a multiple of 1024 does not
+    five = tmp_path / "five.txt"
+    five.write_text("NVIDIA_GB300|2|0|512|20|2 2 0 175.0 16384\n")
+    assert lib.mp_autotune_cache_load(str(five).encode()) == E.MP_OK
+    assert lib.mp_autotune_cache_save(str(out).encode()) == E.MP_OK
+    assert "NVIDIA_GB300|2|0|512|20|2 2 0 175.000000 16384" in out.read_text()
+    five.write_text("NVIDIA_GB300|2|0|512|20|2 2 0 175.0 1000\n")
+    assert lib.mp_autotune_cache_load(str(five).encode()) == E.MP_ERR_INVALID_ARG
 
 
 def test_binding_refuses_cpu_tensors(lib):

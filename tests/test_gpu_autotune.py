@@ -68,7 +68,8 @@ def test_autotune_znorm_filter_choice(mp):
     T = torch.from_numpy(s.T).cuda()
     kw, times = mp.autotune(T, s.m, s.excl, "znorm", force=True)
     assert kw["variant"] in (mp.MP_VARIANT_FAST_FILTER, mp.MP_VARIANT_FAST)
-    assert len(times) == 2 and all(t > 0 for t in times), times
+    assert kw["tile_rows"] in (0, 16384, 4096)
+    assert len(times) == 6 and all(t > 0 for t in times), times  # filter on / off x 3 tile heights
     P, I = mp.acamp(T, s.m, s.excl, **kw)
     torch.cuda.synchronize()
     rows = np.random.default_rng(5).choice(s.N, 150, replace=False)
@@ -77,3 +78,50 @@ def test_autotune_znorm_filter_choice(mp):
                  P_ref=ref[0], I_ref=ref[1], P2=ref[2], label=f"tuned z {kw}")
     with pytest.raises(mp.MPError):
         mp.acamp(T, s.m, s.excl, variant=mp.MP_VARIANT_TALL)
+
+
+def _cache_key(mp, N, m, dist_code, dtype=0, p=2.0):
+    """The autotuning cache key of a problem class (device name, dist, dtype,
+    m, floor(log2 N), p), as the library writes it."""
+    name = torch.cuda.get_device_name().replace(" ", "_").replace("|", "_")
+    return f"{name}|{dist_code}|{dtype}|{m}|{N.bit_length() - 1}|{p:.6g}"
+
+
+def test_cached_tile_rows_in_calls_and_batches(mp, tmp_path):
+    """A cached choice with a tile height (here loaded from a cache file:
+    the z-normalised kernel without its filter at 4,096 rows per tile) is
+    what MP_VARIANT_CACHED runs, in a single call and for the z-normalised
+    series of a batch plan: bit for bit the explicit options' result, which
+    passes the parity rules; without a cache entry CACHED is AUTO."""
+    s = W.small("walk", 60_000, 64, 45, dtype=np.float32)
+    e = W.small("walk", 30_000, 64, 46, dtype=np.float32)  # a Euclidean series in the same batch
+    T = torch.from_numpy(s.T).cuda()
+    path = tmp_path / "cache.txt"
+    path.write_text(f"{_cache_key(mp, s.N, s.m, mp.MP_DIST_ZNORM)} {mp.MP_VARIANT_FAST} 0 1.0 4096\n")
+    mp.autotune_cache_load(str(path))
+    Pc, Ic = mp.acamp(T, s.m, s.excl, variant=mp.MP_VARIANT_CACHED)
+    Pe, Ie = mp.acamp(T, s.m, s.excl, variant=mp.MP_VARIANT_FAST, tile_rows=4096)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(Pc.cpu().numpy(), Pe.cpu().numpy())
+    np.testing.assert_array_equal(Ic.cpu().numpy(), Ie.cpu().numpy())
+    rows = np.random.default_rng(6).choice(s.N, 150, replace=False)
+    ref = oracle.brute_rows(s.T, s.m, s.excl, rows, "znorm")
+    parity.check(s.T, s.m, s.excl, "znorm", 2.0, Pc.cpu().numpy(), Ic.cpu().numpy(), 1e-5, rows=rows,
+                 P_ref=ref[0], I_ref=ref[1], P2=ref[2], label="cached tile rows")
+    plan = mp.BatchPlan([e.n, s.n], [e.m, s.m], ["euclid", "znorm"], [e.excl, s.excl],
+                        variant=mp.MP_VARIANT_CACHED)
+    P, I = plan.run(torch.from_numpy(np.concatenate([e.T, s.T])).cuda())
+    torch.cuda.synchronize()
+    o = plan.out_offsets
+    np.testing.assert_array_equal(P.cpu().numpy()[o[1]:o[2]], Pe.cpu().numpy())
+    np.testing.assert_array_equal(I.cpu().numpy()[o[1]:o[2]], Ie.cpu().numpy())
+    plan.close()
+    # another problem class has no entry: CACHED runs as AUTO
+    u = W.small("walk", 20_000, 40, 47, dtype=np.float32)
+    Tu = torch.from_numpy(u.T).cuda()
+    a1 = mp.acamp(Tu, u.m, u.excl, variant=mp.MP_VARIANT_CACHED)
+    a0 = mp.acamp(Tu, u.m, u.excl)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(a1[0].cpu().numpy(), a0[0].cpu().numpy())
+    with pytest.raises(mp.MPError):
+        mp.aamp(Tu, u.m, u.excl, tile_rows=4096)  # the two-stream / generic kernels have fixed tiles
