@@ -238,7 +238,6 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
     // done in chunk 0); blocks of 8 rows keep every window 16-byte aligned.
     const int nchunks_cta = Hs > 1 ? (Hs - 1 + Z_RC - 1) / Z_RC : 1;
     int ulast = 0;
-    int skip = 0, backoff = 1;  // filter: blocks to run tracked without a filter pass; next skip length
     for (int c = 0; c < nchunks_cta; ++c) {
         const int u0c = c * Z_RC;
         __syncthreads();  // the previous chunk is done with shared memory
@@ -403,9 +402,7 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                 }
                 const float *tra = thr_r + ulb, *trb = trb_base + ulb;
                 const float *tca = thr_ca + v2_cpos(jb + ulb), *tcb = thr_cb + v2_cpos(jb + ulb);
-                if (FILTER && skip > 0) {
-                    --skip;
-                } else if (FILTER) {
+                if (FILTER) {
                     // ---- filter pass: the covariance steps and one running minimum of the
                     // block's scores per stream against the loosest threshold of the rows
                     // and columns they feed; the warp replays the block tracked (from the
@@ -480,10 +477,6 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                             cl[2 * p2] = make_float2(l.x, l.y);
                             cl[2 * p2 + 1] = make_float2(l.z, l.w);
                         }
-                        skip = backoff;
-                        backoff = backoff < 32 ? 2 * backoff : 32;
-                    } else {
-                        backoff = 1;
                     }
                 }
                 if (track) {
