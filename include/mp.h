@@ -108,10 +108,15 @@ typedef enum {
                                  /* Algorithm 2's raw sums (see below)               */
     MP_VARIANT_ZF = 6,           /* ablation, z-normalised only, FP32 or FP64 sweep:  */
                                  /* raw sums compared through F (Sec. 4.3)           */
-    MP_VARIANT_CACHED = 7        /* the autotuner's cached choice for this problem    */
+    MP_VARIANT_CACHED = 7,       /* the autotuner's cached choice for this problem    */
                                  /* class (kernel, reanchor, tile_rows) if present,  */
                                  /* else AUTO; in a batch plan, each z-normalised    */
                                  /* series' cached tile_rows                         */
+    MP_VARIANT_FAST_FILTER_BOUND = 8 /* z-normalised kernel, block filter on a looser */
+                                 /* bound (the block's largest 1/sqrt(S)): one packed */
+                                 /* operation per cell pair instead of two; faster   */
+                                 /* for i.i.d.-like data, slower on random walks;    */
+                                 /* same results bit for bit                         */
 } mp_variant;
 
 typedef struct mp_options {
@@ -388,7 +393,8 @@ mp_status mp_anytime_destroy(mp_anytime *a);
  * divide m into at most 8 blocks, each distinct interval once; the tall-tile
  * kernel for m >= 512; for the z-normalised distance its kernel with and
  * without the filter, each at the default tile height and at 16,384 and 4,096
- * rows per tile where those are shorter than the default and than N)
+ * rows per tile where those are shorter than the default and than N, and with
+ * the looser filter bound at the default tile height)
  * on the caller's series, each candidate once to warm up and once timed (the
  * sweep kernel alone, CUDA events on `stream`; the call synchronises it).
  * slice_cells = 0 times the whole sweep; slice_cells > 0 only the first

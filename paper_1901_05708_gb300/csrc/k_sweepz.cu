@@ -5,7 +5,7 @@
 
 namespace mpk {
 
-template <int MODE, bool FILTER>
+template <int MODE, int FILTER>
 static cudaError_t launch(const SweepZArgs &a, size_t smem, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(sweepz_kernel<MODE, FILTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
@@ -14,12 +14,14 @@ static cudaError_t launch(const SweepZArgs &a, size_t smem, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t sweepz_launch(int mode, bool filter, const SweepZArgs &a, size_t smem, cudaStream_t st) {
+cudaError_t sweepz_launch(int mode, int filter, const SweepZArgs &a, size_t smem, cudaStream_t st) {
     switch (mode) {
-        case K_Z: return filter ? launch<K_Z, true>(a, smem, st) : launch<K_Z, false>(a, smem, st);
-        case K_P1: return launch<K_P1, false>(a, smem, st);
-        case K_P3: return launch<K_P3, false>(a, smem, st);
-        default: return filter ? launch<K_P2, true>(a, smem, st) : launch<K_P2, false>(a, smem, st);
+        case K_Z:
+            return filter == 2 ? launch<K_Z, 2>(a, smem, st) : filter ? launch<K_Z, 1>(a, smem, st)
+                                                                     : launch<K_Z, 0>(a, smem, st);
+        case K_P1: return launch<K_P1, 0>(a, smem, st);
+        case K_P3: return launch<K_P3, 0>(a, smem, st);
+        default: return filter ? launch<K_P2, 1>(a, smem, st) : launch<K_P2, 0>(a, smem, st);
     }
 }
 

@@ -146,7 +146,7 @@ mp_status check_problem(Problem &pb, const void *T, const double *P, const int64
         return fail(MP_ERR_INVALID_ARG, "precision %d", pb.opt.precision);
     if (pb.opt.reanchor < 0) return fail(MP_ERR_INVALID_ARG, "reanchor %d < 0", pb.opt.reanchor);
     if (pb.opt.polish != 0 && pb.opt.polish != 1) return fail(MP_ERR_INVALID_ARG, "polish %d", pb.opt.polish);
-    if (pb.opt.variant < MP_VARIANT_AUTO || pb.opt.variant > MP_VARIANT_CACHED)
+    if (pb.opt.variant < MP_VARIANT_AUTO || pb.opt.variant > MP_VARIANT_FAST_FILTER_BOUND)
         return fail(MP_ERR_INVALID_ARG, "variant %d", pb.opt.variant);
     if (pb.opt.tile_rows < 0 || pb.opt.tile_rows % 1024 != 0 || pb.opt.tile_rows > (1 << 30))
         return fail(MP_ERR_INVALID_ARG, "tile_rows %d: 0 or a positive multiple of 1024", pb.opt.tile_rows);
@@ -290,7 +290,7 @@ mp_status run_tall(const Problem &pb, const Layout &L, char *ws, cudaStream_t st
     if (a.tiles <= 0) return MP_OK;
     const int kind = kind_of(pb.dist, pb.p);
     SweepEvents ev(st);
-    return launched(mpk::sweepz_launch(kind, kind == mpk::K_P2 && pb.N >= FILTER_MIN_N, a, mpk::sweepz_smem_bytes(), st),
+    return launched(mpk::sweepz_launch(kind, kind == mpk::K_P2 && pb.N >= FILTER_MIN_N ? 1 : 0, a, mpk::sweepz_smem_bytes(), st),
                     "tall sweep launch");
 }
 
@@ -386,6 +386,8 @@ mp_status check_call(Problem &pb, const void *T, const double *P, const int64_t 
         return fail(MP_ERR_UNSUPPORTED, "the F comparison is Sec. 4.3's, for the z-normalised distance");
     if (v == MP_VARIANT_TALL && !tall_applies(pb))
         return fail(MP_ERR_UNSUPPORTED, "the tall-tile kernel is the FP32 sweep for p in {1, 2, 3}");
+    if (v == MP_VARIANT_FAST_FILTER_BOUND && !z32)
+        return fail(MP_ERR_UNSUPPORTED, "the bound filter is the FP32 z-normalised kernel's");
     if (pb.opt.tile_rows != 0) {
         const bool zfast = z32 && v != MP_VARIANT_ZRAW && v != MP_VARIANT_ZF && !getenv_generic();
         const bool tall = !z32 && pb.dist != MP_DIST_ZNORM && pb.opt.precision == MP_PREC_FP32 && !fast_path_ok(pb) &&
@@ -501,8 +503,9 @@ mp_status run(Problem &pb, const void *T, double *P, int64_t *I, void *ws, size_
                 za.S = pb.opt.tile_rows > 0 ? pb.opt.tile_rows : mpk::z_rows_per_tile(pb.m, true);
                 za.tiles = mpk::z_prefix(za.L, za.nb, za.S);
                 if (za.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", za.tiles);
-                const bool filter = pb.opt.variant == MP_VARIANT_FAST_FILTER ||
-                                    (pb.opt.variant == MP_VARIANT_AUTO && pb.N >= FILTER_MIN_N);
+                const int filter = pb.opt.variant == MP_VARIANT_FAST_FILTER_BOUND ? 2
+                                   : (pb.opt.variant == MP_VARIANT_FAST_FILTER ||
+                                      (pb.opt.variant == MP_VARIANT_AUTO && pb.N >= FILTER_MIN_N)) ? 1 : 0;
                 e = za.tiles > 0 ? mpk::sweepz_launch(mpk::K_Z, filter, za, mpk::sweepz_smem_bytes(), st)
                                  : cudaSuccess;
             } else if (pb.dist == MP_DIST_ZNORM) {
@@ -1686,6 +1689,7 @@ mp_status mp_autotune(int dist, const void *T, int dtype, int64_t n, int32_t m, 
             cands[nc++] = {MP_VARIANT_FAST_FILTER, 0, t};
             cands[nc++] = {MP_VARIANT_FAST, 0, t};
         }
+        cands[nc++] = {MP_VARIANT_FAST_FILTER_BOUND, 0, 0};  // the looser, cheaper filter bound
     }
     if (nc <= 1) {  // nothing to choose
         if (nc == 1) {
@@ -1798,7 +1802,8 @@ mp_status mp_autotune_cache_load(const char *path) {
         char key[300];
         TuneEntry t;
         const int got = sscanf(line, "%299s %d %d %lf %d", key, &t.variant, &t.reanchor, &t.ms, &t.tile_rows);
-        if ((got != 4 && got != 5) || t.variant < MP_VARIANT_AUTO || t.variant > MP_VARIANT_TALL || t.reanchor < 0 ||
+        if ((got != 4 && got != 5) || t.variant < MP_VARIANT_AUTO ||
+            (t.variant > MP_VARIANT_TALL && t.variant != MP_VARIANT_FAST_FILTER_BOUND) || t.reanchor < 0 ||
             t.tile_rows < 0 || t.tile_rows % 1024 != 0) {
             fclose(f);
             return fail(MP_ERR_INVALID_ARG, "%s:%d: malformed entry", path, lineno);

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(Z_NT, 2) sweepz_batch_kernel(const BatchData d
             za.m = sr->m;
         }
         __syncthreads();
-        sweepz_tile<MODE, false>(za, tile.band, tile.rt, smem);
+        sweepz_tile<MODE, 0>(za, tile.band, tile.rt, smem);
         __syncthreads();
     }
 }

@@ -23,8 +23,9 @@ cudaError_t sweep2_p13_launch(int kind, const Sweep2Args &a, size_t smem, cudaSt
 int *sweep2_p13_error_word();
 
 // k_sweepz.cu: tall float-float tiles (mode K_Z: z-normalised; K_P2, K_P1, K_P3:
-// long Euclidean / p-norm windows) and the batch queue of z-normalised series
-cudaError_t sweepz_launch(int mode, bool filter, const SweepZArgs &a, size_t smem, cudaStream_t st);
+// long Euclidean / p-norm windows) and the batch queue of z-normalised series;
+// filter 0 none, 1 the exact row-minimum filter, 2 (K_Z) the partner-scale bound
+cudaError_t sweepz_launch(int mode, int filter, const SweepZArgs &a, size_t smem, cudaStream_t st);
 cudaError_t batchz_setup(size_t smem, int *ctas_per_sm);
 cudaError_t batchz_launch(int grid, size_t smem, const BatchData &d, const BatchQueue &q, cudaStream_t st);
 int *sweepz_error_word();

@@ -119,7 +119,13 @@ __device__ __forceinline__ float2 z_term(float2 x) {
     } else return __fmul2_rn(x, x);
 }
 
-template <int MODE, bool FILTER>
+// FILTER: 0 no block filter; 1 the filter on each row's exact minimum
+// 1 + inv_i min_d (ch + cl) inv_j; 2 (z-normalised only) the filter on the
+// looser bound 1 + inv_i max_j(inv_j) min(0, min_d (ch + cl)) with the largest
+// 1 / sqrt(S) of the block's 15 partner windows (one packed operation per cell
+// pair instead of two; it pays where the windows' spreads vary little between
+// neighbours, as for i.i.d. data, and loses on random walks).
+template <int MODE, int FILTER>
 __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band, long long rt,
                                             unsigned char *smem) {
     constexpr bool ZN = MODE == K_Z;
@@ -414,10 +420,35 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                             make_float4(cl[2 * p2].x, cl[2 * p2].y, cl[2 * p2 + 1].x, cl[2 * p2 + 1].y);
                     }
                     float bma = NONE, bmb = NONE;
+                    // FILTER == 2: the largest 1 / sqrt(S) of the block's 15 partner windows
+                    float ima = 0.f, imb = 0.f;
+                    if constexpr (ZN && FILTER == 2) {
+                        ima = max3f(WI[1].x, WI[2].x, WI[3].x);
+                        imb = max3f(WI[1].y, WI[2].y, WI[3].y);
+#pragma unroll
+                        for (int x = 4; x < 16; x += 2) {
+                            ima = max3f(ima, WI[x].x, WI[x + 1].x);
+                            imb = max3f(imb, WI[x].y, WI[x + 1].y);
+                        }
+                    }
 #pragma unroll
                     for (int ul = 1; ul <= Z_D; ++ul) {
                         step(ulb + ul, WF, WG, ul);
-                        if constexpr (ZN) {
+                        if constexpr (ZN && FILTER == 2) {
+                            // q = 1 + (ch + cl) inv_i inv_j >= 1 + min(0, min_d (ch + cl)) inv_i inv_max
+                            // (flat partners have inv = NaN, which the maximum skips)
+                            float rma = 0.f, rmb = 0.f;
+#pragma unroll
+                            for (int d = 0; d < Z_D; d += 2) {
+                                const float2 va = add2(ch[d], cl[d]);
+                                const float2 vb = add2(ch[d + 1], cl[d + 1]);
+                                rma = min3f(rma, va.x, vb.x);
+                                rmb = min3f(rmb, va.y, vb.y);
+                            }
+                            const float2 iI = II[ulb + ul];
+                            bma = fminf(bma, fmaf(rma * ima, iI.x, 1.f));
+                            bmb = fminf(bmb, fmaf(rmb * imb, iI.y, 1.f));
+                        } else if constexpr (ZN) {
                             // q = 1 + (ch + cl) inv_i inv_j and inv_i > 0 is common to the
                             // row: its minimum is 1 + inv_i min_d (ch + cl) inv_j, two packed
                             // operations per cell pair instead of three (flat windows have
@@ -573,7 +604,7 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
     }
 }
 
-template <int MODE, bool FILTER>
+template <int MODE, int FILTER>
 __global__ void __launch_bounds__(Z_NT, 2) sweepz_kernel(const SweepZArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     long long band, rt;

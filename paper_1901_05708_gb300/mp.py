@@ -30,7 +30,7 @@ MP_F32, MP_F64 = 0, 1
 MP_PREC_FP32, MP_PREC_FP64 = 0, 1
 MP_DIST_EUCLID, MP_DIST_PNORM, MP_DIST_ZNORM = 0, 1, 2
 (MP_VARIANT_AUTO, MP_VARIANT_FAST_FILTER, MP_VARIANT_FAST, MP_VARIANT_GENERIC, MP_VARIANT_TALL, MP_VARIANT_ZRAW,
- MP_VARIANT_ZF, MP_VARIANT_CACHED) = range(8)
+ MP_VARIANT_ZF, MP_VARIANT_CACHED, MP_VARIANT_FAST_FILTER_BOUND) = range(9)
 
 EXPORTS = ("mp_options_default", "mp_workspace_size", "mp_aamp", "mp_pnorm", "mp_acamp",
            "mp_sync_status", "mp_last_error", "mp_status_string", "mp_version", "mp_launch_count",
@@ -165,7 +165,8 @@ def options(precision: str = "fp32", reanchor: int = 0, polish: bool = True,
     filter (the z-normalised kernel with / without its filter for acamp); MP_VARIANT_GENERIC;
     MP_VARIANT_TALL; MP_VARIANT_ZRAW: Algorithm 2's raw-sum form, an ablation (acamp only);
     MP_VARIANT_ZF: the same raw sums compared through Sec. 4.3's F, an ablation (acamp only);
-    MP_VARIANT_CACHED: the autotuner's cached choice if there is one.  tile_rows: rows per tile of
+    MP_VARIANT_CACHED: the autotuner's cached choice if there is one; MP_VARIANT_FAST_FILTER_BOUND: the
+    z-normalised kernel's filter on a looser, cheaper bound (acamp only).  tile_rows: rows per tile of
     the tall-tile kernels (0: default; else a multiple of 1024)."""
     o = Options()
     load().mp_options_default(ctypes.byref(o))

@@ -82,7 +82,7 @@ def test_argument_checks_need_no_gpu(lib):
     o.precision = 9
     assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG
     lib.mp_options_default(ctypes.byref(o))
-    o.variant = mp.MP_VARIANT_CACHED + 1
+    o.variant = mp.MP_VARIANT_FAST_FILTER_BOUND + 1
     assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG             # no such variant
     lib.mp_options_default(ctypes.byref(o))
     o.tile_rows = 1000
@@ -96,6 +96,8 @@ def test_argument_checks_need_no_gpu(lib):
     assert _call_aamp(lib, opt=o) == E.MP_ERR_UNSUPPORTED             # the raw-sum form is Algorithm 2's
     o.variant = mp.MP_VARIANT_ZF
     assert _call_aamp(lib, opt=o) == E.MP_ERR_UNSUPPORTED             # the F comparison is Sec. 4.3's
+    o.variant = mp.MP_VARIANT_FAST_FILTER_BOUND
+    assert _call_aamp(lib, opt=o) == E.MP_ERR_UNSUPPORTED             # the bound filter is the z kernel's
     o.variant = mp.MP_VARIANT_GENERIC                                   # the z-normalised distance has no generic kernel
     vp = ctypes.c_void_p
     assert lib.mp_acamp(vp(0x1000), 0, 100, 10, 2, vp(0x2000), vp(0x3000), vp(0x10000), 1 << 30,
@@ -195,7 +197,7 @@ def test_autotune_cache_files_need_no_gpu(lib, tmp_path):
     assert lib.mp_autotune_cache_load(str(tmp_path / "missing.txt").encode()) == E.MP_ERR_INVALID_ARG
     o = mp.Options()
     lib.mp_options_default(ctypes.byref(o))
-    o.variant = mp.MP_VARIANT_CACHED + 1
+    o.variant = mp.MP_VARIANT_FAST_FILTER_BOUND + 1
     assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG
     # five-field entries (with tile_rows) load too; a tile_rows that is not a multiple of 1024 does not
     five = tmp_path / "five.txt"

@@ -98,3 +98,31 @@ def test_znorm_row_form_is_within_the_filter_margin():
         worst = max(worst, diff / margin)
         assert float(q_f) - margin <= float(clear_tag(np.array([qmin], f32))[0]), trial
     assert worst < 0.5, worst  # the margin is at least twice what rounding and tags need
+
+
+def test_znorm_partner_scale_bound_is_conservative():
+    """The z-normalised filter's cheaper bound (MP_VARIANT_FAST_FILTER_BOUND):
+    with c = fl(ch + cl) and the block's largest partner scale inv_max,
+    fl(fma(min(0, min_d c) inv_max, inv_i, 1)) minus the filter's margin is at
+    most every tagged q of the row (q = fma(cl, w, fma(ch, w, 1)), w = inv_i
+    inv_j, inv_j <= inv_max), whatever the partners' spread."""
+    rng = np.random.default_rng(2)
+    for trial in range(400):
+        nd = 8
+        S_i = rng.uniform(0.5, 50.0) * 512
+        S_j = rng.uniform(0.5, 50.0) * 512 * rng.uniform(0.9, 1.1, nd) ** rng.choice([1, 5])
+        rho = rng.uniform(-1.0, 1.0, nd) ** rng.choice([1, 3, 9])
+        cov = -rho * np.sqrt(S_i * S_j)
+        ch = cov.astype(f32)
+        cl = (cov - ch.astype(np.float64)).astype(f32) + f32(rng.normal(0, 1e-3)) * np.abs(ch) * f32(1e-4)
+        inv_i = np.array([1.0 / np.sqrt(S_i)], f32)
+        inv_j = (1.0 / np.sqrt(S_j)).astype(f32)
+        wv = (inv_i.astype(np.float64) * inv_j).astype(f32)
+        q_t = fma32(cl, wv, fma32(ch, wv, np.ones(nd, f32)))
+        c = (ch.astype(np.float64) + cl).astype(f32)
+        rmin = np.array([min(0.0, float(c.min()))], f32)
+        imax = np.array([inv_j.max()], f32)
+        prod = (rmin.astype(np.float64) * imax).astype(f32)
+        b = fma32(prod, inv_i, np.ones(1, f32))[0]
+        margin = max(2e-5, abs(float(b)) * 2.0 ** -18)
+        assert float(b) - margin <= float(clear_tag(np.array([q_t.min()], f32))[0]), trial

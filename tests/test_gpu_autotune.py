@@ -67,9 +67,10 @@ def test_autotune_znorm_filter_choice(mp):
     s = W.small("walk", 210_000, 64, 44, dtype=np.float32)
     T = torch.from_numpy(s.T).cuda()
     kw, times = mp.autotune(T, s.m, s.excl, "znorm", force=True)
-    assert kw["variant"] in (mp.MP_VARIANT_FAST_FILTER, mp.MP_VARIANT_FAST)
+    assert kw["variant"] in (mp.MP_VARIANT_FAST_FILTER, mp.MP_VARIANT_FAST, mp.MP_VARIANT_FAST_FILTER_BOUND)
     assert kw["tile_rows"] in (0, 16384, 4096)
-    assert len(times) == 6 and all(t > 0 for t in times), times  # filter on / off x 3 tile heights
+    # filter on / off x 3 tile heights, and the bound filter
+    assert len(times) == 7 and all(t > 0 for t in times), times
     P, I = mp.acamp(T, s.m, s.excl, **kw)
     torch.cuda.synchronize()
     rows = np.random.default_rng(5).choice(s.N, 150, replace=False)
@@ -125,3 +126,22 @@ def test_cached_tile_rows_in_calls_and_batches(mp, tmp_path):
     np.testing.assert_array_equal(a1[0].cpu().numpy(), a0[0].cpu().numpy())
     with pytest.raises(mp.MPError):
         mp.aamp(Tu, u.m, u.excl, tile_rows=4096)  # the two-stream / generic kernels have fixed tiles
+
+
+@pytest.mark.parametrize("kind", ["flat", "uniform"])
+def test_bound_filter_is_bit_identical(mp, kind):
+    """MP_VARIANT_FAST_FILTER_BOUND only changes which blocks the z-normalised
+    filter skips: its profile equals the exact filter's and the unfiltered
+    kernel's bit for bit (flat windows included)."""
+    s = W.small(kind, 210_000, 64, 48, dtype=np.float32)  # a random walk with a flat run, or i.i.d. values
+    T = torch.from_numpy(s.T).cuda()
+    out = []
+    for v in (mp.MP_VARIANT_FAST_FILTER_BOUND, mp.MP_VARIANT_FAST_FILTER, mp.MP_VARIANT_FAST):
+        P, I = mp.acamp(T, s.m, s.excl, variant=v)
+        torch.cuda.synchronize()
+        out.append((P.cpu().numpy(), I.cpu().numpy()))
+    for P, I in out[1:]:
+        np.testing.assert_array_equal(out[0][0], P)
+        np.testing.assert_array_equal(out[0][1], I)
+    with pytest.raises(mp.MPError):
+        mp.aamp(T, s.m, s.excl, variant=mp.MP_VARIANT_FAST_FILTER_BOUND)

@@ -84,3 +84,23 @@ def test_tall_kernel_on_short_windows(mp):
     Pr, Ir = oracle.aamp(T.astype(np.float64), 1_100, 200)
     np.testing.assert_array_equal(It, Ir)
     np.testing.assert_array_equal(Pt, Pr)
+
+
+@pytest.mark.parametrize("dist,p,tile_rows", [("euclid", 2.0, 4096), ("pnorm", 1.0, 1024), ("znorm", 2.0, 1024),
+                                              ("znorm", 2.0, 8192)])
+def test_tile_rows(mp, dist, p, tile_rows):
+    """mp_options.tile_rows on the tall-tile kernels: tiles shorter than the
+    default (here down to 1,024 rows, below 8m, so several tiles per band and
+    ragged last tiles) give the oracle's profile within the parity rules."""
+    m = 600 if dist != "znorm" else 200
+    s = W.small("motif", 30_000, m, 63, dtype=np.float32)
+    rows = np.unique(np.concatenate([np.random.default_rng(7).choice(s.N, 60, replace=False), [0, s.N - 1]]))
+    ref = oracle.brute_rows(s.T, s.m, s.excl, rows, dist, p)
+    kw = {"tile_rows": tile_rows}
+    if dist != "znorm":
+        kw["variant"] = 4  # the tall-tile kernel
+    P, I = run(mp, s.T, s.m, s.excl, dist, p, **kw)
+    parity.check(s.T, s.m, s.excl, dist, p, P, I, RTOL32, rows=rows, P_ref=ref[0], I_ref=ref[1], P2=ref[2],
+                 label=f"{dist} tile_rows={tile_rows}")
+    x = np.arange(s.N)
+    assert np.all(I >= 0) and np.all(np.abs(I - x) > s.excl)
