@@ -42,7 +42,7 @@ FP32_LANES_PER_SM = 128
 CSRC = os.path.join(ROOT, "paper_1901_05708_gb300", "csrc")
 # the sources that make up each workload's sweep kernel (their hash names the kernel version)
 SWEEP_SOURCES = {
-    "euclid": ["mp_device.cuh", "mp_sweep2.cuh", "k_sweep2.cu"],
+    "euclid": ["mp_device.cuh", "mp_sweep2.cuh", "k_sweep2.cu", "k_sweep2_tall.cu"],
     "pnorm": ["mp_device.cuh", "mp_sweep2.cuh", "k_sweep2_p13.cu"],
     "znorm": ["mp_device.cuh", "mp_sweep2.cuh", "mp_sweep_z2.cuh", "k_sweepz.cu"],
 }
@@ -392,6 +392,8 @@ def main():
     ap.add_argument("--shard", action="store_true",
                     help="split one series' diagonals over the ranks and merge (strong scaling); "
                          "default: every rank its own series (weak scaling)")
+    ap.add_argument("--tile-rows", type=int, default=0,
+                    help="mp_options.tile_rows of the FP32 sweep (0: the library's choice)")
     ap.add_argument("--fp64-diagonals", type=int, default=8192,
                     help="also time the FP64 sweep on this many diagonals (0: skip)")
     args = ap.parse_args()
@@ -437,6 +439,8 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     kw = {"precision": args.precision}
+    if args.tile_rows:
+        kw["tile_rows"] = args.tile_rows
     if args.k_range:
         kw["k_range"] = tuple(args.k_range)
     if shard_range is not None:
@@ -579,6 +583,8 @@ def main():
                     "d2h_bytes_per_step": int(N * 16), "ms_per_step": e2e_ms}}
     if args.k_range:
         line["config"]["k_range"] = list(args.k_range)
+    if args.tile_rows:
+        line["config"]["tile_rows"] = args.tile_rows
     if shard_range is not None:
         line["config"]["parallelism"] = f"diagonal ranges over {ws} ranks, merged by two MIN all-reduces"
         line["config"]["rank0_diagonals"] = list(shard_range)

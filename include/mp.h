@@ -71,7 +71,10 @@ typedef enum { MP_DIST_EUCLID = 0, MP_DIST_PNORM = 1, MP_DIST_ZNORM = 2 } mp_dis
 /* Kernel of the FP32 sweep.  Euclidean / p-norm, AUTO: the two-stream kernel
  * where it applies (FP32 input, m a multiple of 32 up to 416, p in {1, 2, 3},
  * default re-anchor interval), with the block filter for p = 2 and
- * N >= 200,000; else,
+ * N >= 200,000, in tiles of 16,384 rows (each stream walks 8,192 rows in
+ * staged sub-tiles of 768 and pays the O(m) anchor once) where that leaves at
+ * least 16,384 tiles and p != 3, else of 2,048 rows (mp_options.tile_rows
+ * overrides; the results differ only by FP32 rounding); else,
  * for m >= 512 and p in {1, 2, 3} with float32 input (or where the generic
  * kernel's shared memory does not fit m), the tall-tile kernel; else the
  * generic kernel.  (The tall kernel does not re-anchor within a tile, so for
@@ -126,13 +129,18 @@ typedef struct mp_options {
     int32_t polish;       /* 1 (default): P[i] recomputed in FP64 as d(i, I[i])   */
                           /* 0: P is the sweep's own (FP32 or FP64) value          */
     int32_t variant;      /* FP32 sweep kernel, mp_variant (default MP_VARIANT_AUTO) */
-    int32_t tile_rows;    /* rows per tile of the tall-tile kernels (the FP32      */
-                          /* z-normalised kernel and MP_VARIANT_TALL): 0 (default) */
-                          /* = max(65536, 8m) for z-normalised, max(8192, 8m) for  */
-                          /* tall; else a multiple of 1024.  Taller tiles pay the  */
-                          /* O(m) anchor less often and carry the FP32 state over  */
-                          /* more rows; shorter ones give short series more tiles. */
-                          /* Must be 0 for the other kernels (MP_ERR_UNSUPPORTED). */
+    int32_t tile_rows;    /* rows per tile of the two-stream kernel and of the     */
+                          /* tall-tile kernels (the FP32 z-normalised kernel and   */
+                          /* MP_VARIANT_TALL).  0 (default): for the two-stream   */
+                          /* kernel the tallest of 16384, 8192 and 4096 rows that */
+                          /* leaves at least 4096 tiles, else 2048; for the z-    */
+                          /* normalised kernel max(65536, 8m); for the tall kernel */
+                          /* max(8192, 8m).  Else a multiple of 2048 (two-stream) */
+                          /* or of 1024 (tall-tile kernels).  Taller tiles pay the */
+                          /* O(m) anchor less often; shorter ones give short      */
+                          /* series more tiles.  The two-stream kernel re-anchors */
+                          /* every m/Q rows whatever the tile height.  Must be 0  */
+                          /* for the generic kernel (MP_ERR_UNSUPPORTED).          */
     int64_t k_begin;      /* sweep only diagonals k >= k_begin (default 0)        */
     int64_t k_end;        /* ... and k < k_end (<= 0 means no upper bound).       */
                           /* Disjoint ranges computed separately and merged with  */
@@ -388,7 +396,10 @@ mp_status mp_anytime_destroy(mp_anytime *a);
 /* ---- Autotuning -------------------------------------------------------------
  *
  * mp_autotune times the kernel variants that apply to a problem (the
- * two-stream kernel with and without the filter; the generic kernel at its
+ * two-stream kernel with and without the filter, and, with the filter for
+ * p = 2 or without it for p = 1, 3, at the tile height its default does not
+ * take: 2,048 rows where the default is tall, 16,384 where the default is
+ * 2,048 and the tall tiles still number at least 1,216; the generic kernel at its
  * default re-anchor interval and at intervals of 16, 32 and 64 rows that
  * divide m into at most 8 blocks, each distinct interval once; the tall-tile
  * kernel for m >= 512; for the z-normalised distance its kernel with and

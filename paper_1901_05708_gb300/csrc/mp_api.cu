@@ -227,11 +227,11 @@ int kind_of(int dist, double p) {
 bool fast_path_applies(const Problem &pb) {
     const bool lp = pb.dist == MP_DIST_EUCLID || (pb.dist == MP_DIST_PNORM && kind_of(pb.dist, pb.p) != mpk::K_PG);
     return lp && pb.dtype == MP_F32 && pb.m % 32 == 0 && pb.opt.reanchor == 0 &&
-           mpk::sweep2_smem_bytes(pb.m, mpk::V2_QMAX) <= mpk::V2_SMEM_MAX;
+           mpk::sweep2_smem_bytes(pb.m, mpk::V2_R) <= mpk::V2_SMEM_MAX;
 }
 
 bool fast_path_ok(const Problem &pb) {
-    if (pb.opt.variant == MP_VARIANT_GENERIC) return false;
+    if (pb.opt.variant == MP_VARIANT_GENERIC || pb.opt.variant == MP_VARIANT_TALL) return false;
     return fast_path_applies(pb) && !getenv_generic();
 }
 
@@ -247,6 +247,28 @@ mp_status launched(cudaError_t e, const char *what) {
 // series and on the p-norm kernels (periodic data) it fails too often.
 constexpr long long FILTER_MIN_N = 200000;
 
+// Rows per tile of the two-stream sweep: the caller's tile_rows, else tall
+// tiles of V2_TALL_R rows (eight one-step tiles; the O(m) anchor from the
+// definition is paid once per 16,384 rows instead of once per 2,048) where
+// they still leave V2_TALL_MIN_TILES tiles, else one-step tiles of V2_R rows.
+// Measured on a GB300 (sweep kernel, n = 2^20): +5% for p = 2 at m = 256, +9%
+// at m = 384, +2% at m = 128, +10% on i.i.d. data, +4% for p = 1, none for
+// p = 3 (kept at one step), +8% at n = 2^21.  On shorter series tall tiles
+// lose (-6% at n = 2^19, -13% at 2^18): the resident tiles then span many
+// bands whose first blocks meet open thresholds, and each sub-tile pays its
+// staging and barriers.  The choice depends on the problem only, never on the
+// device, so results do not change between GPUs.
+constexpr long long V2_TALL_R = 8 * mpk::V2_R;
+constexpr long long V2_TALL_MIN_TILES = 16384;
+constexpr long long V2_TALL_TUNE_TILES = 1216;  // the autotuner tries tall tiles from four waves of 2 x 152 CTAs
+long long sweep2_rows(const Problem &pb, long long L, long long nb) {
+    if (pb.opt.tile_rows > 0) return pb.opt.tile_rows;
+    if (kind_of(pb.dist, pb.p) != mpk::K_P3 && mpk::v2_prefix(L, nb, V2_TALL_R) >= V2_TALL_MIN_TILES &&
+        mpk::sweep2_smem_bytes(pb.m, V2_TALL_R) <= mpk::V2_SMEM_MAX)
+        return V2_TALL_R;
+    return mpk::V2_R;
+}
+
 mp_status run_sweep2(const Problem &pb, const Layout &L, char *ws, cudaStream_t st) {
     mpk::Sweep2Args a{};
     a.t = reinterpret_cast<const float *>(ws + L.hi);
@@ -260,10 +282,14 @@ mp_status run_sweep2(const Problem &pb, const Layout &L, char *ws, cudaStream_t 
     a.B = pb.m / a.Q;
     a.L = pb.N - pb.k_first;
     a.nb = (pb.k_end - pb.k_first + mpk::V2_KW - 1) / mpk::V2_KW;
-    a.tiles = mpk::v2_prefix(a.L, a.nb);
+    a.R = sweep2_rows(pb, a.L, a.nb);
+    a.tiles = mpk::v2_prefix(a.L, a.nb, a.R);
     if (a.tiles > 0x7fffffffLL) return fail(MP_ERR_UNSUPPORTED, "too many tiles (%lld)", a.tiles);
     if (a.tiles <= 0) return MP_OK;
-    const size_t smem = mpk::sweep2_smem_bytes(a.m, mpk::V2_QMAX);
+    const size_t smem = mpk::sweep2_smem_bytes(a.m, a.R);
+    if (smem > mpk::V2_SMEM_MAX)
+        return fail(MP_ERR_UNSUPPORTED, "tile_rows %lld: the two-stream tile needs %zu bytes of shared memory",
+                    a.R, smem);
     const int kind = kind_of(pb.dist, pb.p);
     SweepEvents ev(st);
     if (kind != mpk::K_P2) return launched(mpk::sweep2_p13_launch(kind, a, smem, st), "two-stream sweep launch");
@@ -390,10 +416,14 @@ mp_status check_call(Problem &pb, const void *T, const double *P, const int64_t 
         return fail(MP_ERR_UNSUPPORTED, "the bound filter is the FP32 z-normalised kernel's");
     if (pb.opt.tile_rows != 0) {
         const bool zfast = z32 && v != MP_VARIANT_ZRAW && v != MP_VARIANT_ZF && !getenv_generic();
-        const bool tall = !z32 && pb.dist != MP_DIST_ZNORM && pb.opt.precision == MP_PREC_FP32 && !fast_path_ok(pb) &&
-                          use_tall(pb);
-        if (!zfast && !tall)
-            return fail(MP_ERR_UNSUPPORTED, "tile_rows applies to the tall-tile kernels only");
+        const bool lp32 = !z32 && pb.dist != MP_DIST_ZNORM && pb.opt.precision == MP_PREC_FP32;
+        const bool two = lp32 && fast_path_ok(pb);
+        const bool tall = lp32 && !two && use_tall(pb);
+        if (two && pb.opt.tile_rows % mpk::V2_R != 0)
+            return fail(MP_ERR_UNSUPPORTED, "tile_rows %d: the two-stream kernel's tiles are multiples of %d rows",
+                        pb.opt.tile_rows, mpk::V2_R);
+        if (!zfast && !tall && !two)
+            return fail(MP_ERR_UNSUPPORTED, "tile_rows applies to the two-stream and tall-tile kernels only");
     }
     return MP_OK;
 }
@@ -669,7 +699,8 @@ mp_status mp_sync_status(void *stream) {
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     // the error word of every translation unit that holds kernels
-    int *words[] = {mpk::device_error_ptr(), mpk::sweep2_p2_error_word(), mpk::sweep2_p13_error_word(),
+    int *words[] = {mpk::device_error_ptr(), mpk::sweep2_p2_error_word(), mpk::sweep2_tall_error_word(),
+                    mpk::sweep2_p13_error_word(),
                     mpk::sweepz_error_word(), mpk::batch2_error_word(), mpk::generic_error_word()};
     int bits = 0;
     for (int *w : words) {
@@ -1012,7 +1043,7 @@ static mp_status batch_plan_build(const mp_batch_desc *desc, const mp_options *o
             }
             b.zS = static_cast<int>(zS);
             batch_tiles(q[qi], si, L, mpk::Z_KW, b.zS);
-        } else if (b.m % 32 == 0 && mpk::sweep2_smem_bytes(b.m, mpk::V2_QMAX) <= mpk::V2_SMEM_MAX &&
+        } else if (b.m % 32 == 0 && mpk::sweep2_smem_bytes(b.m, mpk::V2_R) <= mpk::V2_SMEM_MAX &&
                    (p2 || pl->genp_kind == mpk::K_P1 || pl->genp_kind == mpk::K_P3)) {
             qi = p2 ? mp_batch_plan::Q_FAST2 : mp_batch_plan::Q_FASTP;
             batch_tiles(q[qi], si, L, mpk::V2_KW, mpk::V2_R);
@@ -1057,7 +1088,7 @@ static mp_status batch_plan_build(const mp_batch_desc *desc, const mp_options *o
         pl->tiles[qi].reserve(q[qi].size());
         for (auto &t : q[qi]) pl->tiles[qi].push_back(t.second);
         if (qi == mp_batch_plan::Q_FAST2 || qi == mp_batch_plan::Q_FASTP)
-            pl->smem[qi] = mpk::sweep2_smem_bytes(std::max(qmax_m[qi], 32), mpk::V2_QMAX);
+            pl->smem[qi] = mpk::sweep2_smem_bytes(std::max(qmax_m[qi], 32), mpk::V2_R);
         else if (qi == mp_batch_plan::Q_Z) pl->smem[qi] = mpk::sweepz_smem_bytes();
         else pl->smem[qi] = mpk::sweep_smem_bytes(mpk::BATCH_GEN_R, std::max(qmax_m[qi], 1), std::max(qmax_Q[qi], 1), false);
         if (!pl->tiles[qi].empty() && pl->smem[qi] > 227 * 1024) {
@@ -1660,9 +1691,20 @@ mp_status mp_autotune(int dist, const void *T, int dtype, int64_t n, int32_t m, 
     if (pb.dist != MP_DIST_ZNORM && pb.opt.precision == MP_PREC_FP32) {
         Problem q = pb;
         q.opt.reanchor = 0;
+        q.opt.tile_rows = 0;
         if (fast_path_applies(q)) {
-            if (kind_of(pb.dist, pb.p) == mpk::K_P2) cands[nc++] = {MP_VARIANT_FAST_FILTER, 0, 0};
+            const int kind = kind_of(pb.dist, pb.p);
+            if (kind == mpk::K_P2) cands[nc++] = {MP_VARIANT_FAST_FILTER, 0, 0};
             cands[nc++] = {MP_VARIANT_FAST, 0, 0};
+            // the tile height the default does not take: one-step tiles where it
+            // takes tall ones, tall ones where they still fill a few waves
+            const long long L = pb.N - pb.k_first, nb = (pb.k_end - pb.k_first + mpk::V2_KW - 1) / mpk::V2_KW;
+            const long long R0 = sweep2_rows(q, L, nb);
+            const int variant = kind == mpk::K_P2 ? MP_VARIANT_FAST_FILTER : MP_VARIANT_FAST;
+            if (R0 != mpk::V2_R) cands[nc++] = {variant, 0, static_cast<int>(mpk::V2_R)};
+            else if (mpk::v2_prefix(L, nb, V2_TALL_R) >= V2_TALL_TUNE_TILES &&
+                     mpk::sweep2_smem_bytes(pb.m, V2_TALL_R) <= mpk::V2_SMEM_MAX)
+                cands[nc++] = {variant, 0, static_cast<int>(V2_TALL_R)};
         }
         // the generic kernel with its default interval and with 16, 32, 64 rows,
         // each effective interval (choose_block) once

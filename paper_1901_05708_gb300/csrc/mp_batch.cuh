@@ -115,9 +115,10 @@ __global__ void __launch_bounds__(V2_NT, 2) sweep2_batch_kernel(const BatchData 
             sa.m = sr->m;
             sa.Q = v2_ring_blocks(KIND);
             sa.B = sr->m / sa.Q;
+            sa.R = V2_R;  // one-step tiles (the queue's tiles are V2_R rows)
         }
         __syncthreads();
-        sweep2_tile<KIND, FILTER>(sa, tile.band, tile.rt, smem);
+        sweep2_tile<KIND, FILTER, false>(sa, tile.band, tile.rt, smem);
         __syncthreads();
     }
 }

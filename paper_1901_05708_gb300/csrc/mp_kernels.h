@@ -14,11 +14,17 @@
 
 namespace mpk {
 
-// k_sweep2.cu: the two-stream Euclidean sweep, with or without the block filter
+// k_sweep2.cu: the two-stream Euclidean sweep, with or without the block
+// filter, in one-step tiles (a.R == V2_R; taller tiles go to k_sweep2_tall.cu)
 cudaError_t sweep2_p2_launch(bool filter, const Sweep2Args &a, size_t smem, cudaStream_t st);
 int *sweep2_p2_error_word();
 
-// k_sweep2_p13.cu: the two-stream p-norm sweep for p = 1 (kind K_P1) and p = 3 (K_P3)
+// k_sweep2_tall.cu: the same in tall tiles (a.R > V2_R)
+cudaError_t sweep2_p2_tall_launch(bool filter, const Sweep2Args &a, size_t smem, cudaStream_t st);
+int *sweep2_tall_error_word();
+
+// k_sweep2_p13.cu: the two-stream p-norm sweep for p = 1 (kind K_P1) and p = 3
+// (K_P3), one-step or tall tiles
 cudaError_t sweep2_p13_launch(int kind, const Sweep2Args &a, size_t smem, cudaStream_t st);
 int *sweep2_p13_error_word();
 

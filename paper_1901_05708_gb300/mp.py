@@ -167,7 +167,8 @@ def options(precision: str = "fp32", reanchor: int = 0, polish: bool = True,
     MP_VARIANT_ZF: the same raw sums compared through Sec. 4.3's F, an ablation (acamp only);
     MP_VARIANT_CACHED: the autotuner's cached choice if there is one; MP_VARIANT_FAST_FILTER_BOUND: the
     z-normalised kernel's filter on a looser, cheaper bound (acamp only).  tile_rows: rows per tile of
-    the tall-tile kernels (0: default; else a multiple of 1024)."""
+    the two-stream kernel (a multiple of 2048) and of the tall-tile kernels (a multiple of 1024); 0: the
+    default."""
     o = Options()
     load().mp_options_default(ctypes.byref(o))
     o.precision = {"fp32": MP_PREC_FP32, "fp64": MP_PREC_FP64}[precision]

@@ -90,7 +90,9 @@ def test_argument_checks_need_no_gpu(lib):
     o.tile_rows = -1024
     assert _call_aamp(lib, opt=o) == E.MP_ERR_INVALID_ARG
     o.tile_rows = 2048
-    assert _call_aamp(lib, opt=o) == E.MP_ERR_UNSUPPORTED             # the two-stream kernel has fixed tiles
+    assert _call_aamp(lib, opt=o) == E.MP_ERR_UNSUPPORTED             # m = 10: the generic kernel's tiles are fixed
+    o.tile_rows = 3072
+    assert _call_aamp(lib, m=32, opt=o) == E.MP_ERR_UNSUPPORTED       # two-stream tiles: multiples of 2048 rows
     lib.mp_options_default(ctypes.byref(o))
     o.variant = mp.MP_VARIANT_ZRAW
     assert _call_aamp(lib, opt=o) == E.MP_ERR_UNSUPPORTED             # the raw-sum form is Algorithm 2's

@@ -125,7 +125,7 @@ def test_cached_tile_rows_in_calls_and_batches(mp, tmp_path):
     torch.cuda.synchronize()
     np.testing.assert_array_equal(a1[0].cpu().numpy(), a0[0].cpu().numpy())
     with pytest.raises(mp.MPError):
-        mp.aamp(Tu, u.m, u.excl, tile_rows=4096)  # the two-stream / generic kernels have fixed tiles
+        mp.aamp(Tu, u.m, u.excl, tile_rows=4096)  # m = 40: the generic kernel, whose tiles are fixed
 
 
 @pytest.mark.parametrize("kind", ["flat", "uniform"])

@@ -209,6 +209,40 @@ def test_integer_long_series_bit_exact(mp, excl):
     np.testing.assert_array_equal(P, Pr)
 
 
+@pytest.mark.parametrize("tile_rows", [4096, 6144, 16384])
+def test_two_stream_tall_tiles_bit_exact(mp, tile_rows):
+    """Tall tiles of the two-stream kernel (mp_options.tile_rows, a multiple of
+    2,048): each stream walks several staged sub-tiles, carrying its sums and
+    the ring of block sums from one to the next, and the last tile of each
+    band is ragged.  On integer data every FP32 value is exact, so P and I
+    equal the FP64 oracle (Algorithms 1 and 3) for p = 2 with and without the
+    block filter, p = 1 and p = 3."""
+    rng = np.random.default_rng(910 + tile_rows)
+    T = rng.integers(-8, 9, 30_000).astype(np.float32)
+    m, excl = 64, 16
+    T64 = T.astype(np.float64)
+    cases = (("euclid", 2.0, mp.MP_VARIANT_FAST_FILTER), ("euclid", 2.0, mp.MP_VARIANT_FAST),
+             ("pnorm", 1.0, mp.MP_VARIANT_FAST), ("pnorm", 3.0, mp.MP_VARIANT_FAST))
+    for dist, p, variant in cases:
+        Pr, Ir = oracle.aamp(T64, m, excl) if dist == "euclid" else oracle.pnorm(T64, m, excl, p)
+        P, I = run(mp, T, m, excl, dist, p, variant=variant, tile_rows=tile_rows)
+        np.testing.assert_array_equal(I, Ir, err_msg=f"{dist} p={p} variant={variant}")
+        if p == 3.0:  # the final cube root: CUDA's and the C library's pow may differ by an ulp
+            np.testing.assert_allclose(P, Pr, rtol=4e-16, atol=0)
+        else:
+            np.testing.assert_array_equal(P, Pr, err_msg=f"{dist} p={p} variant={variant}")
+
+
+@pytest.mark.parametrize("dist,p", [("euclid", 2.0), ("pnorm", 1.0), ("pnorm", 3.0)])
+def test_two_stream_tall_tiles_walk(mp, dist, p):
+    """A random walk with a planted motif through 8,192-row tiles of the
+    two-stream kernel (4 sub-tiles of 768 rows per stream): every row passes
+    the parity rules against brute force."""
+    s = W.small("motif", 20_000, 128, 912, dtype=np.float32)
+    P, I = run(mp, s.T, s.m, s.excl, dist, p, variant=mp.MP_VARIANT_FAST, tile_rows=8192)
+    parity.check(s.T, s.m, s.excl, dist, p, P, I, RTOL32, label=f"tall two-stream {dist} p={p}")
+
+
 def test_long_walk_filter_kernel(mp):
     """A 300,000-point random walk with a planted motif (filter kernel): sampled
     rows by brute force, the motif rows included."""
