@@ -46,9 +46,9 @@ constexpr int Z_D = 8;                // diagonals per thread
 constexpr int Z_KW = Z_NT * Z_D;      // diagonals per band
 constexpr int Z_S = 8192;             // rows per tile of the long-window p-norm modes (at least; max(Z_S, 8m))
 constexpr int Z_SZ = 65536;           // rows per tile of the z-normalised sweep (at least)
-constexpr int Z_RC = 512;             // rows per stream per chunk
+constexpr int Z_RC = 768;             // rows per stream per chunk
 
-// Rows per tile for window length m: max(base, 8m) rounded up to 2 RC, with
+// Rows per tile for window length m: max(base, 8m) rounded up to 1024, with
 // base Z_SZ for the z-normalised sweep (zn) and Z_S for the p-norm modes.  A
 // tile pays one O(m) float-float anchor per stream and carries the state over
 // S / 2 rows: the z-normalised float-float covariance drifts little (measured
@@ -58,7 +58,7 @@ constexpr int Z_RC = 512;             // rows per stream per chunk
 // their tiles stay shorter.
 __host__ __device__ inline long long z_rows_per_tile(long long m, bool zn) {
     long long S = 8 * m;
-    S = (S + 2 * Z_RC - 1) / (2 * Z_RC) * (2 * Z_RC);
+    S = (S + 1023) / 1024 * 1024;
     const long long base = zn ? Z_SZ : Z_S;
     return S < base ? base : S;
 }
