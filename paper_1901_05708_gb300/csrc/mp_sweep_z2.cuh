@@ -434,14 +434,21 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
 #pragma unroll
                     for (int ul = 1; ul <= Z_D; ++ul) {
                         step(ulb + ul, WF, WG, ul);
+                        // every 4th row the z-normalised state is folded (Fast2Sum) before its
+                        // bound, which then needs the high word alone (the low word is below
+                        // half an ulp of it, inside the margin); the folds fall on the same rows
+                        // as in the tracked pass, so the block's end state does not change
+                        constexpr bool kFold = ZN;
+                        const bool fold4 = kFold && (ul & 3) == 0;
+                        if (fold4) renorm();
                         if constexpr (ZN && FILTER == 2) {
                             // q = 1 + (ch + cl) inv_i inv_j >= 1 + min(0, min_d (ch + cl)) inv_i inv_max
                             // (flat partners have inv = NaN, which the maximum skips)
                             float rma = 0.f, rmb = 0.f;
 #pragma unroll
                             for (int d = 0; d < Z_D; d += 2) {
-                                const float2 va = add2(ch[d], cl[d]);
-                                const float2 vb = add2(ch[d + 1], cl[d + 1]);
+                                const float2 va = fold4 ? ch[d] : add2(ch[d], cl[d]);
+                                const float2 vb = fold4 ? ch[d + 1] : add2(ch[d + 1], cl[d + 1]);
                                 rma = min3f(rma, va.x, vb.x);
                                 rmb = min3f(rmb, va.y, vb.y);
                             }
@@ -456,8 +463,10 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                             float rma = NONE, rmb = NONE;
 #pragma unroll
                             for (int d = 0; d < Z_D; d += 2) {
-                                const float2 va = fma2(cl[d], WI[ul + d], z_mul(ch[d], WI[ul + d]));
-                                const float2 vb = fma2(cl[d + 1], WI[ul + d + 1], z_mul(ch[d + 1], WI[ul + d + 1]));
+                                const float2 va = fold4 ? z_mul(ch[d], WI[ul + d])
+                                                        : fma2(cl[d], WI[ul + d], z_mul(ch[d], WI[ul + d]));
+                                const float2 vb = fold4 ? z_mul(ch[d + 1], WI[ul + d + 1])
+                                                        : fma2(cl[d + 1], WI[ul + d + 1], z_mul(ch[d + 1], WI[ul + d + 1]));
                                 rma = min3f(rma, va.x, vb.x);
                                 rmb = min3f(rmb, va.y, vb.y);
                             }
@@ -473,7 +482,7 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                                 bmb = min3f(bmb, qa.y, qb.y);
                             }
                         }
-                        if ((ul & 1) == 0 && (!r4 || (ul & 3) == 0)) renorm();
+                        if (!fold4 && (ul & 1) == 0 && (!r4 || (ul & 3) == 0)) renorm();
                     }
                     if constexpr (ZN) {
                         // the row form rounds differently from the tracked pass's q

@@ -12,7 +12,8 @@ exact arithmetic:
 * z-normalised sweep: the row form 1 + inv_i * min_d((ch + cl) * inv_j) differs
   from the tracked pass's q = fma(cl, w, fma(ch, w, 1)), w = inv_i * inv_j, by
   far less than the margin max(2e-5, |q| 2^-18) the filter subtracts, plus the
-  7 units in the last place a tag can move q.
+  7 units in the last place a tag can move q; so does the folded form
+  1 + inv_i * min_d(fl(ch + cl) * inv_j) of every 4th row.
 """
 import numpy as np
 
@@ -98,6 +99,38 @@ def test_znorm_row_form_is_within_the_filter_margin():
         worst = max(worst, diff / margin)
         assert float(q_f) - margin <= float(clear_tag(np.array([qmin], f32))[0]), trial
     assert worst < 0.5, worst  # the margin is at least twice what rounding and tags need
+
+
+def test_znorm_folded_row_form_is_within_the_filter_margin():
+    """On every 4th row the z-normalised filter pass folds the float-float
+    state first (Fast2Sum: h = fl(ch + cl), l = cl - (h - ch)) and bounds the
+    row from the high word alone, 1 + inv_i min_d h inv_j, while the tracked
+    pass scores the unfolded words.  The difference stays well inside the
+    margin the filter subtracts, tags included."""
+    rng = np.random.default_rng(3)
+    worst = 0.0
+    for trial in range(400):
+        nd = 8
+        S_i = rng.uniform(0.5, 50.0) * 512
+        S_j = rng.uniform(0.5, 50.0, nd) * 512
+        rho = rng.uniform(-1.0, 1.0, nd) ** rng.choice([1, 3, 9])
+        cov = -rho * np.sqrt(S_i * S_j)
+        ch = cov.astype(f32)
+        # the low word before a fold: the rounding of ch plus a few rows of increments
+        cl = (cov - ch.astype(np.float64)).astype(f32) + f32(rng.normal(0, 1.0)) * np.abs(ch) * f32(rng.choice([1e-4, 1e-2]))
+        inv_i = np.array([1.0 / np.sqrt(S_i)], f32)
+        inv_j = (1.0 / np.sqrt(S_j)).astype(f32)
+        wv = (inv_i.astype(np.float64) * inv_j).astype(f32)
+        q_t = fma32(cl, wv, fma32(ch, wv, np.ones(nd, f32)))      # tracked pass, unfolded words
+        h = (ch.astype(np.float64) + cl).astype(f32)                # Fast2Sum's high word
+        v = (h.astype(np.float64) * inv_j).astype(f32)
+        q_f = fma32(np.array([v.min()], f32), inv_i, np.ones(1, f32))[0]
+        qmin = q_t.min()
+        margin = max(2e-5, abs(float(q_f)) * 2.0 ** -18)
+        ulp = np.spacing(np.abs(qmin).astype(f32))
+        worst = max(worst, (abs(float(q_f) - float(qmin)) + 7 * float(ulp)) / margin)
+        assert float(q_f) - margin <= float(clear_tag(np.array([qmin], f32))[0]), trial
+    assert worst < 0.5, worst
 
 
 def test_znorm_partner_scale_bound_is_conservative():
