@@ -271,15 +271,16 @@ __device__ __forceinline__ float2 v2_sub(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, one rounding
 }
 
-// acc + term(x) for both streams: x^2 (one packed FMA), |x| (two FADDs with an
-// absolute-value operand), |x|^3 = |x| x^2 (a packed multiply and two FMAs).
+// acc + term(x) for both streams: x^2 (one packed FMA), |x| (one packed add, the
+// absolute values taken as operand modifiers), |x|^3 = |x| x^2 (a packed multiply
+// and a packed FMA).  Each lane rounds as the scalar operation would.
 template <int KIND>
 __device__ __forceinline__ float2 v2_acc(float2 x, float2 acc) {
     if constexpr (KIND == K_P1) {
-        return make_float2(acc.x + fabsf(x.x), acc.y + fabsf(x.y));
+        return __fadd2_rn(acc, make_float2(fabsf(x.x), fabsf(x.y)));
     } else if constexpr (KIND == K_P3) {
         const float2 x2 = __fmul2_rn(x, x);
-        return make_float2(fmaf(fabsf(x.x), x2.x, acc.x), fmaf(fabsf(x.y), x2.y, acc.y));
+        return __ffma2_rn(make_float2(fabsf(x.x), fabsf(x.y)), x2, acc);
     } else {
         return fma2(x, x, acc);
     }

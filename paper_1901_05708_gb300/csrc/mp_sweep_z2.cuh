@@ -115,7 +115,7 @@ __device__ __forceinline__ float2 z_term(float2 x) {
     if constexpr (MODE == K_P1) return make_float2(fabsf(x.x), fabsf(x.y));
     else if constexpr (MODE == K_P3) {
         const float2 x2 = __fmul2_rn(x, x);
-        return make_float2(fabsf(x.x) * x2.x, fabsf(x.y) * x2.y);
+        return __fmul2_rn(make_float2(fabsf(x.x), fabsf(x.y)), x2);  // lanes round as scalar products
     } else return __fmul2_rn(x, x);
 }
 
