@@ -226,6 +226,11 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
     }
 
     float ca[Z_D], cb[Z_D];
+    // the filter's maximum over columns 1..8 of the next fast block: its
+    // columns 9..16 read with the previous block (fast blocks are contiguous;
+    // thresholds only decrease, so an older read is looser)
+    bool group_valid = false;
+    float gca = 0.f, gcb = 0.f;
 #pragma unroll
     for (int d = 0; d < Z_D; ++d) { ca[d] = NONE; cb[d] = NONE; }
 
@@ -498,13 +503,31 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                     tmb = max3f(tmb, trb[4], trb[5]);
                     tma = max3f(tma, tra[6], tra[7]);
                     tmb = max3f(tmb, trb[6], trb[7]);
-                    tma = max3f(tma, tra[8], tca[1]);
-                    tmb = max3f(tmb, trb[8], tcb[1]);
-#pragma unroll
-                    for (int x = 2; x < 2 * Z_D; x += 2) {
-                        tma = max3f(tma, tca[x + (x >> 3)], tca[x + 1 + ((x + 1) >> 3)]);
-                        tmb = max3f(tmb, tcb[x + (x >> 3)], tcb[x + 1 + ((x + 1) >> 3)]);
+                    if (!group_valid) {  // columns 1..8 at padded offsets 1..7, 9
+                        gca = max3f(tca[1], tca[2], tca[3]);
+                        gcb = max3f(tcb[1], tcb[2], tcb[3]);
+                        gca = max3f(gca, tca[4], tca[5]);
+                        gcb = max3f(gcb, tcb[4], tcb[5]);
+                        gca = max3f(gca, tca[6], tca[7]);
+                        gcb = max3f(gcb, tcb[6], tcb[7]);
+                        gca = fmaxf(gca, tca[9]);
+                        gcb = fmaxf(gcb, tcb[9]);
                     }
+                    // columns 9..16 at padded offsets 10..16, 18 (16 is the next block's first)
+                    float uga = max3f(tca[10], tca[11], tca[12]), ugb = max3f(tcb[10], tcb[11], tcb[12]);
+                    uga = max3f(uga, tca[13], tca[14]);
+                    ugb = max3f(ugb, tcb[13], tcb[14]);
+                    uga = max3f(uga, tca[15], tca[16]);
+                    ugb = max3f(ugb, tcb[15], tcb[16]);
+                    uga = fmaxf(uga, tca[18]);
+                    ugb = fmaxf(ugb, tcb[18]);
+                    tma = max3f(tma, tra[8], gca);
+                    tmb = max3f(tmb, trb[8], gcb);
+                    tma = fmaxf(tma, uga);
+                    tmb = fmaxf(tmb, ugb);
+                    gca = uga;
+                    gcb = ugb;
+                    group_valid = true;
                     // a tagged score is at least the score with its tag bits cleared
                     track = __any_sync(__activemask(), __int_as_float(__float_as_int(bma) & tag_mask) <= tma ||
                                                            __int_as_float(__float_as_int(bmb) & tag_mask) <= tmb);
