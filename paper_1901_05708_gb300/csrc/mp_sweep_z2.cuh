@@ -95,7 +95,8 @@ __device__ __forceinline__ bool z_decode(const SweepZArgs &a, long long t, long 
 
 __host__ __device__ inline size_t sweepz_thr_bytes() {
     const size_t nc = v2_cpos(Z_KW + Z_RC + 16);  // column thresholds, per stream
-    return ((2 * (Z_RC + 8) + 2 * nc) * sizeof(float) + 15) / 16 * 16;
+    // + 3 floats in front: the row thresholds start 3 floats past a 16-byte boundary
+    return ((3 + 2 * (Z_RC + 8) + 2 * nc) * sizeof(float) + 15) / 16 * 16;
 }
 
 inline size_t sweepz_smem_bytes() {
@@ -146,11 +147,14 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
     float2 *IF = JI + njs;
     float2 *IG = IF + (Z_RC + 16);
     float2 *II = IG + (Z_RC + 16);
-    float *thr_r = reinterpret_cast<float *>(II + (Z_RC + 16));  // [2 (RC + 8)]: stream a rows, stream b rows
+    // [2 (RC + 8)]: stream a rows, stream b rows; 3 floats past a 16-byte boundary, so
+    // that the thresholds of chunk rows 8g+1 .. 8g+4 and 8g+5 .. 8g+8 are 16-byte loads
+    float *thr_base = reinterpret_cast<float *>(II + (Z_RC + 16));
+    float *thr_r = thr_base + 3;
     const int ncs = v2_cpos(Z_KW + Z_RC + 16);
     float *thr_ca = thr_r + 2 * (Z_RC + 8);
     float *thr_cb = thr_ca + ncs;
-    float4 *zsave = reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(thr_r) + sweepz_thr_bytes());
+    float4 *zsave = reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(thr_base) + sweepz_thr_bytes());
 
     const int jb = tid * Z_D;
     const long long kt = k0 + jb;
@@ -498,11 +502,15 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                         bma = bma - fmaxf(2e-5f, fabsf(bma) * 0x1p-18f);
                         bmb = bmb - fmaxf(2e-5f, fabsf(bmb) * 0x1p-18f);
                     }
-                    float tma = max3f(tra[1], tra[2], tra[3]), tmb = max3f(trb[1], trb[2], trb[3]);
-                    tma = max3f(tma, tra[4], tra[5]);
-                    tmb = max3f(tmb, trb[4], trb[5]);
-                    tma = max3f(tma, tra[6], tra[7]);
-                    tmb = max3f(tmb, trb[6], trb[7]);
+                    const float4 ra0 = *reinterpret_cast<const float4 *>(tra + 1);
+                    const float4 ra1 = *reinterpret_cast<const float4 *>(tra + 5);
+                    const float4 rb0 = *reinterpret_cast<const float4 *>(trb + 1);
+                    const float4 rb1 = *reinterpret_cast<const float4 *>(trb + 5);
+                    float tma = max3f(ra0.x, ra0.y, ra0.z), tmb = max3f(rb0.x, rb0.y, rb0.z);
+                    tma = max3f(tma, ra0.w, ra1.x);
+                    tmb = max3f(tmb, rb0.w, rb1.x);
+                    tma = max3f(tma, ra1.y, ra1.z);
+                    tmb = max3f(tmb, rb1.y, rb1.z);
                     if (!group_valid) {  // columns 1..8 at padded offsets 1..7, 9
                         gca = max3f(tca[1], tca[2], tca[3]);
                         gcb = max3f(tcb[1], tcb[2], tcb[3]);
@@ -521,8 +529,8 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                     ugb = max3f(ugb, tcb[15], tcb[16]);
                     uga = fmaxf(uga, tca[18]);
                     ugb = fmaxf(ugb, tcb[18]);
-                    tma = max3f(tma, tra[8], gca);
-                    tmb = max3f(tmb, trb[8], gcb);
+                    tma = max3f(tma, ra1.w, gca);
+                    tmb = max3f(tmb, rb1.w, gcb);
                     tma = fmaxf(tma, uga);
                     tmb = fmaxf(tmb, ugb);
                     gca = uga;
