@@ -43,7 +43,7 @@ CSRC = os.path.join(ROOT, "paper_1901_05708_gb300", "csrc")
 # the sources that make up each workload's sweep kernel (their hash names the kernel version)
 SWEEP_SOURCES = {
     "euclid": ["mp_device.cuh", "mp_sweep2.cuh", "k_sweep2.cu", "k_sweep2_tall.cu"],
-    "pnorm": ["mp_device.cuh", "mp_sweep2.cuh", "k_sweep2_p13.cu"],
+    "pnorm": ["mp_device.cuh", "mp_sweep2.cuh", "k_sweep2_p13.cu", "mp_sweep_z2.cuh", "k_sweepz.cu"],
     "znorm": ["mp_device.cuh", "mp_sweep2.cuh", "mp_sweep_z2.cuh", "k_sweepz.cu"],
 }
 
@@ -174,7 +174,7 @@ def oracle_sample(series: W.Series, target_s: float = 12.0):
     K = min(256, max(1, series.N - k0))
     while True:
         t0 = time.perf_counter()
-        sweep((k0, k0 + K))
+        ref = sweep((k0, k0 + K))
         dt = time.perf_counter() - t0
         if dt >= 0.5 * target_s or K >= series.N - k0:
             break
@@ -182,7 +182,41 @@ def oracle_sample(series: W.Series, target_s: float = 12.0):
     cells = sum(series.N - k for k in range(k0, k0 + K))
     return {"value": cells / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{series.name}: diagonals {k0}..{k0 + K - 1} ({cells:.3e} cells) in {dt:.2f} s",
-            "cpu": cpu_model(), "seconds": dt, "cells": cells}
+            "cpu": cpu_model(), "seconds": dt, "cells": cells, "k_range": (k0, k0 + K), "ref": ref}
+
+
+def slice_error(torch, mp, series: W.Series, T, dname: str, cb: dict) -> dict:
+    """The FP32 profile of the oracle's timed diagonal slice, raw (polish off)
+    and polished, against the oracle's FP64 partial profile of the same slice,
+    over every row the slice reaches: the largest relative error of P (with
+    the oracle's P at that row), the largest error in units of the FP32
+    acceptance bound 1e-5 P_ref + atol (atol = 1e-5 m^(1/p) sd(diff T) for
+    the pure and p-norm distances, 1e-5 sqrt(m) for the z-normalised one; at
+    most 1 is within it), and the rows whose index differs (a near-tie can
+    legitimately differ)."""
+    Pr, Ir = cb["ref"]
+    fin = np.isfinite(Pr) & (Pr > 0)
+    rtol = 1e-5
+    if series.dist == W.ZNORM:
+        atol = rtol * math.sqrt(series.m)
+    else:
+        atol = rtol * series.m ** (1.0 / series.p) * float(np.std(np.diff(series.T.astype(np.float64))))
+    out = {"diagonals": list(cb["k_range"]), "rows": int(fin.sum())}
+    for polish in (False, True):
+        P, I = mp.profile(T, series.m, series.excl, dname, series.p, k_range=cb["k_range"], polish=polish)
+        torch.cuda.synchronize()
+        mp.sync_status()
+        P, I = P.cpu().numpy()[fin], I.cpu().numpy()[fin]
+        key = "polished" if polish else "raw"
+        if P.size:
+            err = np.abs(P - Pr[fin])
+            w = int(np.argmax(err / Pr[fin]))
+            out[f"{key}_max_rel_err"] = float(err[w] / Pr[fin][w])
+            out[f"{key}_max_rel_err_at_P"] = float(Pr[fin][w])
+            out[f"{key}_max_over_bound"] = float(np.max(err / (rtol * Pr[fin] + atol)))
+        if polish:
+            out["index_mismatch"] = int(np.sum(I != Ir[fin]))
+    return out
 
 
 def cpu_model() -> str:
@@ -594,6 +628,9 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = oracle_sample(series, target_s=args.ref_seconds)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu")}
+        if args.precision == "fp32" and not args.k_range:
+            # outside the timed regions: the FP32 path's error on the oracle's own slice
+            line["cpu_baseline"]["fp32_error_on_sample"] = slice_error(torch, mp, series, T, dname, cb)
     elif rank == 0:
         line["cpu_baseline"] = None  # timed on rank 0 at N = 1 only
     if rank == 0:

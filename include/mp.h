@@ -68,17 +68,24 @@ typedef enum {
 
 typedef enum { MP_DIST_EUCLID = 0, MP_DIST_PNORM = 1, MP_DIST_ZNORM = 2 } mp_dist;
 
-/* Kernel of the FP32 sweep.  Euclidean / p-norm, AUTO: the two-stream kernel
- * where it applies (FP32 input, m a multiple of 32 up to 416, p in {1, 2, 3},
- * default re-anchor interval), with the block filter for p = 2 and
+/* Kernel of the FP32 sweep.  Euclidean / p-norm, AUTO: for p = 3 with float32
+ * input, the tall-tile kernel, whose p = 3 window sums are error-free (each
+ * is the float-float sum of its FP32 terms |x - y|^3: the re-anchored FP32
+ * kernels keep, until their next anchor, an error of the size of the largest
+ * term met, which on series whose terms span many orders of magnitude puts
+ * small distances far outside the FP32 tolerance; MP_VARIANT_FAST still runs
+ * the two-stream kernel for p = 3, faster, with that caveat).  Otherwise the
+ * two-stream kernel where it applies (FP32 input, m a multiple of 32 up to 416,
+ * p in {1, 2, 3}, default re-anchor interval), with the block filter for p = 2 and
  * N >= 200,000, in tiles of 16,384 rows (each stream walks 8,192 rows in
  * staged sub-tiles of 768 and pays the O(m) anchor once) where that leaves at
  * least 16,384 tiles and p != 3, else of 2,048 rows (mp_options.tile_rows
  * overrides; the results differ only by FP32 rounding); else,
  * for m >= 512 and p in {1, 2, 3} with float32 input (or where the generic
  * kernel's shared memory does not fit m), the tall-tile kernel; else the
- * generic kernel.  (The tall kernel does not re-anchor within a tile, so for
- * short windows its FP32 rounding grows past the tolerance, most for p = 3.)
+ * generic kernel.  (For p = 1 and 2 the tall kernel does not re-anchor within
+ * a tile, so for short windows its FP32 rounding can grow past the tolerance
+ * on near ties.)
  * The z-normalised distance has one FP32 kernel: AUTO takes its block filter
  * for N >= 200,000, FAST_FILTER / FAST force it on / off, GENERIC and TALL do
  * not apply.  The filter only skips candidates that cannot pass, so with or
@@ -281,6 +288,12 @@ typedef struct mp_batch_plan mp_batch_plan;
  * FAST (no block filter) or FAST_FILTER (the filter on the Euclidean
  * two-stream queue).  The tile queues take the series in turn (first tiles of
  * all series, then second tiles, ...), longest tiles first within a turn.
+ * Each series' profile equals its single call (mp_aamp / mp_pnorm / mp_acamp
+ * with the same options) bit for bit, except for p = 3: the batch runs p = 3
+ * series on the re-anchored two-stream or generic kernel (as mp_pnorm with
+ * MP_VARIANT_FAST, or MP_VARIANT_GENERIC where the two-stream kernel does not
+ * apply), not on the error-free tall-tile kernel that mp_pnorm takes by
+ * default, so the caveat of mp_variant on p = 3 applies.
  * desc is not kept.
  * Errors: MP_ERR_INVALID_ARG (desc, sizes, dist, p), MP_ERR_UNSUPPORTED
  * (dtype, options, N_s >= 2^31, more than 2^32 - 1 tiles in a queue, m_s too

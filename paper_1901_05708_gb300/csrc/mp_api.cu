@@ -232,6 +232,8 @@ bool fast_path_applies(const Problem &pb) {
 
 bool fast_path_ok(const Problem &pb) {
     if (pb.opt.variant == MP_VARIANT_GENERIC || pb.opt.variant == MP_VARIANT_TALL) return false;
+    // p = 3: only on request (see p3_exact)
+    if (kind_of(pb.dist, pb.p) == mpk::K_P3 && pb.opt.variant != MP_VARIANT_FAST) return false;
     return fast_path_applies(pb) && !getenv_generic();
 }
 
@@ -332,9 +334,22 @@ bool tall_applies(const Problem &pb) {
     return pb.dist != MP_DIST_ZNORM && kind_of(pb.dist, pb.p) != mpk::K_PG && pb.opt.precision == MP_PREC_FP32;
 }
 
+// p = 3 with float32 input goes to the tall kernel, whose p = 3 sums are
+// error-free (each window sum is the float-float sum of its FP32 terms).  The
+// re-anchored FP32 kernels carry an error of the size of the largest term met
+// since the last anchor: |x|^3 spans many orders of magnitude, and after a
+// high-amplitude stretch leaves the windows a small distance can be off by
+// far more than the FP32 tolerance (measured on the sine-and-motif series,
+// n = 2^18, m = 128: 306 rows off by up to 14% after the polish through the
+// two-stream kernel, whose block sums are re-anchored every m / 4 rows).
+bool p3_exact(const Problem &pb) {
+    return kind_of(pb.dist, pb.p) == mpk::K_P3 && tall_applies(pb) && pb.dtype == MP_F32;
+}
+
 bool use_tall(const Problem &pb) {
     if (pb.opt.variant == MP_VARIANT_TALL) return true;
     if (pb.opt.variant != MP_VARIANT_AUTO || !tall_applies(pb) || getenv_generic()) return false;
+    if (p3_exact(pb)) return true;
     // The tall kernel carries a whole tile without re-anchoring: the rounding of
     // each step's increment accumulates over up to S/2 rows.  An increment is
     // about 1/m of a window sum, so from m = 512 on that stays well inside the
@@ -1688,7 +1703,9 @@ mp_status mp_autotune(int dist, const void *T, int dtype, int64_t n, int32_t m, 
     struct Cand { int variant, reanchor, tile_rows; };
     Cand cands[12];
     int nc = 0;
-    if (pb.dist != MP_DIST_ZNORM && pb.opt.precision == MP_PREC_FP32) {
+    if (p3_exact(pb)) {
+        cands[nc++] = {MP_VARIANT_TALL, 0, 0};  // the one kernel whose p = 3 sums hold the tolerance
+    } else if (pb.dist != MP_DIST_ZNORM && pb.opt.precision == MP_PREC_FP32) {
         Problem q = pb;
         q.opt.reanchor = 0;
         q.opt.tile_rows = 0;

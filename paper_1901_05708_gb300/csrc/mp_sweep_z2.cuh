@@ -336,8 +336,8 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
             ca[j] = NONE;
             cb[j] = NONE;
         };
-        // one covariance step into chunk row ul, partner window offset o
-        // The increments go into the low word only; renorm() folds it into the
+        // one covariance (or p-norm sum) step into chunk row ul, partner window offset o
+        // The increments go into the low word only (p = 3: see below); renorm() folds it into the
         // high word with an error-free Fast2Sum after every second row (every
         // fourth for z-normalised windows of m >= 64, whose increments are small
         // against the covariance), so the low word never holds more than a few
@@ -354,6 +354,24 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                     const float2 e = v2_sub(fi, WF[o + d]), f = v2_sub(gi, WG[o + d]);
                     if constexpr (MODE == K_P2) {
                         cl[d] = fma2(e, e, v2_sub(cl[d], z_mul(f, f)));
+                    } else if constexpr (MODE == K_P3) {
+                        // error-free: |x|^3 spans many orders of magnitude, and a
+                        // rounded increment term(e) - term(f) would leave an error
+                        // of the size of the largest term in the window sum long
+                        // after that term left.  The leaving term comes off the
+                        // high word with Fast2Sum (exact: the window holds it, so
+                        // ch >= term(f) / 2), the entering one goes on with TwoSum,
+                        // and only their rounding errors reach the low word; the
+                        // sum is then the exact sum of the window's FP32 terms to
+                        // float-float precision.
+                        const float2 xf = z_term<MODE>(f), xe = z_term<MODE>(e);
+                        const float2 s1 = v2_sub(ch[d], xf);
+                        const float2 e1 = v2_sub(v2_sub(ch[d], s1), xf);
+                        const float2 s2 = add2(s1, xe);
+                        const float2 bb = v2_sub(s2, s1);
+                        const float2 e2 = add2(v2_sub(s1, v2_sub(s2, bb)), v2_sub(xe, bb));
+                        ch[d] = s2;
+                        cl[d] = add2(cl[d], add2(e1, e2));
                     } else {
                         cl[d] = add2(cl[d], v2_sub(z_term<MODE>(e), z_term<MODE>(f)));
                     }

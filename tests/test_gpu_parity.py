@@ -180,15 +180,17 @@ def test_invalid_arguments(mp):
 @pytest.mark.parametrize("m", [32, 64, 96])
 def test_integer_fast_path_bit_exact(mp, m):
     """The two-stream kernel (m a multiple of 32, FP32 input) on integer data,
-    for p = 2, 1 and 3: every term and partial sum is an integer below 2^24,
-    so P and I equal the oracle exactly, ties included."""
+    for p = 2, 1 and 3 (for p = 3 also the tall-tile kernel, its default):
+    every term and partial sum is an integer below 2^24, so P and I equal the
+    oracle exactly, ties included."""
     rng = np.random.default_rng(900 + m)
     T = rng.integers(-8, 9, 7000).astype(np.float32)
-    for dist, p in (("euclid", 2.0), ("pnorm", 1.0), ("pnorm", 3.0)):
+    for dist, p, variant in (("euclid", 2.0, 0), ("pnorm", 1.0, 0), ("pnorm", 3.0, mp.MP_VARIANT_FAST),
+                             ("pnorm", 3.0, 0)):
         for excl in (0, m // 4):
             Pr, Ir = oracle.brute(T, m, excl, dist, p)
-            P, I = run(mp, T, m, excl, dist, p)
-            np.testing.assert_array_equal(I, Ir, err_msg=f"{dist} p={p} excl={excl}")
+            P, I = run(mp, T, m, excl, dist, p, variant=variant)
+            np.testing.assert_array_equal(I, Ir, err_msg=f"{dist} p={p} excl={excl} variant={variant}")
             if p == 3.0:  # the final cube root: CUDA's and the C library's pow may differ by an ulp
                 np.testing.assert_allclose(P, Pr, rtol=4e-16, atol=0)
             else:
@@ -277,8 +279,9 @@ def test_long_znorm_filter_kernel(mp):
 
 @pytest.mark.parametrize("dist,p", [("euclid", 2.0), ("pnorm", 1.0), ("pnorm", 3.0)])
 def test_fast_and_generic_kernels_agree(mp, monkeypatch, dist, p):
-    """Fast and generic FP32 kernels against the oracle on a series with many
-    bands and row tiles (n = 40,000, m = 64)."""
+    """The default FP32 kernel (two-stream; tall-tile for p = 3) and the
+    generic one against the oracle on a series with many bands and row tiles
+    (n = 40,000, m = 64)."""
     s = W.small("motif", 40_000, 64, 81, dtype=np.float32)
     rows = np.random.default_rng(1).choice(s.N, 400, replace=False)
     ref = oracle.brute_rows(s.T, s.m, s.excl, rows, dist, p)
