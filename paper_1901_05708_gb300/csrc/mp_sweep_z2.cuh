@@ -360,16 +360,20 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                         // of the size of the largest term in the window sum long
                         // after that term left.  The leaving term comes off the
                         // high word with Fast2Sum (exact: the window holds it, so
-                        // ch >= term(f) / 2), the entering one goes on with TwoSum,
-                        // and only their rounding errors reach the low word; the
-                        // sum is then the exact sum of the window's FP32 terms to
-                        // float-float precision.
+                        // ch >= term(f) / 2), the entering one goes on with Fast2Sum
+                        // after ordering the two by size (both are >= 0, so the
+                        // larger value is the larger magnitude; the ordering runs on
+                        // the ALU pipe, a TwoSum would take three more FMA-pipe
+                        // operations), and only their rounding errors reach the low
+                        // word; the sum is then the exact sum of the window's FP32
+                        // terms to float-float precision.
                         const float2 xf = z_term<MODE>(f), xe = z_term<MODE>(e);
                         const float2 s1 = v2_sub(ch[d], xf);
                         const float2 e1 = v2_sub(v2_sub(ch[d], s1), xf);
-                        const float2 s2 = add2(s1, xe);
-                        const float2 bb = v2_sub(s2, s1);
-                        const float2 e2 = add2(v2_sub(s1, v2_sub(s2, bb)), v2_sub(xe, bb));
+                        const float2 hi = make_float2(fmaxf(s1.x, xe.x), fmaxf(s1.y, xe.y));
+                        const float2 lo = make_float2(fminf(s1.x, xe.x), fminf(s1.y, xe.y));
+                        const float2 s2 = add2(hi, lo);
+                        const float2 e2 = v2_sub(lo, v2_sub(s2, hi));
                         ch[d] = s2;
                         cl[d] = add2(cl[d], add2(e1, e2));
                     } else {
