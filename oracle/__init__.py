@@ -163,7 +163,12 @@ def aamp(T, m, excl, raw=False, k_range=(0, _KMAX)):
 
 
 def pnorm(T, m, excl, p, raw=False, k_range=(0, _KMAX)):
-    """Algorithm 3: diagonal sweep with the Lemma 2 update."""
+    """Algorithm 3: diagonal sweep with the Lemma 2 update, in FP64 and, as
+    the algorithm states it, without re-anchoring: where the terms |x - y|^p
+    span many orders of magnitude, a small later sum keeps an absolute error
+    of about 1e-16 times the largest sum met on its diagonal (9.4e-6 relative
+    on one row of the sine-and-motif series at p = 3, next to its flat run);
+    brute_rows, from the definition, is the reference where that matters."""
     T = _t(T)
     P, I = _outputs(T.size - m + 1)
     rc = _load().orc_pnorm(_ptr(T), T.size, m, excl, float(p), int(k_range[0]),
