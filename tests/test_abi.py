@@ -93,6 +93,9 @@ def test_argument_checks_need_no_gpu(lib):
     assert _call_aamp(lib, opt=o) == E.MP_ERR_UNSUPPORTED             # m = 10: the generic kernel's tiles are fixed
     o.tile_rows = 3072
     assert _call_aamp(lib, m=32, opt=o) == E.MP_ERR_UNSUPPORTED       # two-stream tiles: multiples of 2048 rows
+    o.variant = mp.MP_VARIANT_FAST                                      # p = 3 on the two-stream kernel, on request
+    assert lib.mp_pnorm(ctypes.c_void_p(0x1000), 0, 100, 32, 2, 3.0, ctypes.c_void_p(0x2000), ctypes.c_void_p(0x3000),
+                        ctypes.c_void_p(0x10000), 1 << 30, ctypes.byref(o), ctypes.c_void_p(0)) == E.MP_ERR_UNSUPPORTED
     lib.mp_options_default(ctypes.byref(o))
     o.variant = mp.MP_VARIANT_ZRAW
     assert _call_aamp(lib, opt=o) == E.MP_ERR_UNSUPPORTED             # the raw-sum form is Algorithm 2's
