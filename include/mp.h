@@ -410,12 +410,14 @@ mp_status mp_anytime_destroy(mp_anytime *a);
  *
  * mp_autotune times the kernel variants that apply to a problem (the
  * two-stream kernel with and without the filter, and, with the filter for
- * p = 2 or without it for p = 1, 3, at the tile height its default does not
+ * p = 2 or without it for p = 1, at the tile height its default does not
  * take: 2,048 rows where the default is tall, 16,384 where the default is
  * 2,048 and the tall tiles still number at least 1,216; the generic kernel at its
  * default re-anchor interval and at intervals of 16, 32 and 64 rows that
  * divide m into at most 8 blocks, each distinct interval once; the tall-tile
- * kernel for m >= 512; for the z-normalised distance its kernel with and
+ * kernel for m >= 512; for p = 3 with float32 input only the tall-tile
+ * kernel, whose sums hold the FP32 tolerance (nothing to time: it is returned
+ * as the choice); for the z-normalised distance its kernel with and
  * without the filter, each at the default tile height and at 16,384 and 4,096
  * rows per tile where those are shorter than the default and than N, and with
  * the looser filter bound at the default tile height)
