@@ -101,3 +101,49 @@ def test_reanchored_fp32_sums_lose_small_distances():
         s = float(f32(E - F))
         worst = max(worst, abs(s - ref[u]) / ref[u])
     assert worst > 1e-3, worst  # far outside the FP32 tolerance on P^3 (3e-5)
+
+
+def _error_free_walk(x, m, k, rows):
+    i0 = rows.start
+    ch, cl = f32(0), f32(0)
+    for l in range(m):
+        p = term(f32(x[i0 + l] - x[i0 + k + l]))
+        t = f32(ch + p)
+        bb = f32(t - ch)
+        cl = f32(cl + f32(f32(ch - f32(t - bb)) + f32(p - bb)))
+        ch = t
+    sums = []
+    for u, i in enumerate(rows):
+        if u > 0:
+            xe = term(f32(x[i + m - 1] - x[i + k + m - 1]))
+            xf = term(f32(x[i - 1] - x[i + k - 1]))
+            s1 = f32(ch - xf)
+            e1 = f32(f32(ch - s1) - xf)
+            hi, lo = max(s1, xe), min(s1, xe)
+            s2 = f32(hi + lo)
+            e2 = f32(lo - f32(s2 - hi))
+            ch = s2
+            cl = f32(cl + f32(e1 + e2))
+            if u % 2 == 0:
+                t = f32(ch + cl)
+                cl = f32(cl - f32(t - ch))
+                ch = t
+        sums.append(float(ch) + float(cl))
+    return np.array(sums)
+
+
+def test_error_free_p3_sums_single_spike():
+    """A window sum made of one large term: while the spike is in the window
+    the high word is that term (ch = term(f) when it leaves, the edge of
+    Fast2Sum's condition), and after it leaves the sum returns to the small
+    terms' exact sum."""
+    m, k = 64, 300
+    rng = np.random.default_rng(9)
+    x = (rng.normal(0.0, 1e-3, 2000)).astype(f32)
+    x[1000] = f32(40.0)  # |x|^3 = 64,000 against terms of about 1e-9
+    rows = range(900, 1200)
+    ref = exact_window_sums(x, m, k, rows, term)
+    got = _error_free_walk(x, m, k, rows)
+    assert ref.max() > 6e4 and ref[-1] < 1e-6
+    rel = np.abs(got - ref) / ref
+    assert rel.max() < 1e-6, rel.max()
