@@ -336,7 +336,7 @@ bool tall_applies(const Problem &pb) {
 
 // p = 3 with float32 input goes to the tall kernel, whose p = 3 sums are
 // error-free (each window sum is the float-float sum of its FP32 terms).  The
-// re-anchored FP32 kernels carry an error of the size of the largest term met
+// re-anchored FP32 kernels carry the FP32 rounding of the largest sums met
 // since the last anchor: |x|^3 spans many orders of magnitude, and after a
 // high-amplitude stretch leaves the windows a small distance can be off by
 // far more than the FP32 tolerance (measured on the sine-and-motif series,

@@ -356,8 +356,8 @@ __device__ __forceinline__ void sweepz_tile(const SweepZArgs &a, long long band,
                         cl[d] = fma2(e, e, v2_sub(cl[d], z_mul(f, f)));
                     } else if constexpr (MODE == K_P3) {
                         // error-free: |x|^3 spans many orders of magnitude, and a
-                        // rounded increment term(e) - term(f) would leave an error
-                        // of the size of the largest term in the window sum long
+                        // rounded increment term(e) - term(f) would leave the FP32
+                        // rounding of the largest term in the window sum long
                         // after that term left.  The leaving term comes off the
                         // high word with Fast2Sum (exact: the window holds it, so
                         // ch >= term(f) / 2), the entering one goes on with Fast2Sum
