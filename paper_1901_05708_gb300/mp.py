@@ -250,7 +250,11 @@ def aamp(T, m: int, excl: int, *, precision="fp32", reanchor=0, polish=True, k_r
 
 def pnorm(T, m: int, excl: int, p: float, *, precision="fp32", reanchor=0, polish=True,
           k_range=None, variant=0, tile_rows=0, out=None, stream=None):
-    """Matrix profile with the p-norm distance (Algorithm 3)."""
+    """Matrix profile with the p-norm distance (Algorithm 3).  For p = 3 with a
+    float32 series the default FP32 kernel carries error-free window sums
+    (include/mp.h, mp_variant); variant=MP_VARIANT_FAST runs the faster
+    re-anchored two-stream kernel, which can miss the FP32 tolerance on series
+    whose terms |x - y|^3 span many orders of magnitude."""
     return _call("mp_pnorm", MP_DIST_PNORM, T, m, excl, p,
                  options(precision, reanchor, polish, k_range, variant, tile_rows), out, stream)
 
